@@ -1,0 +1,251 @@
+"""FP64 CPU oracle for the meshfree log-likelihood -- TEST INFRASTRUCTURE.
+
+A plain, slow, obviously-correct restatement of the paper's method used only
+to check the CUDA library: the test-suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import it; nothing in the product does.  It
+shares no code with the CUDA path.  Start-up steps use library routines as
+single steps (NumPy/LAPACK SVD, dense solve, symmetric eigensolver); the
+online stage is written out as loops in ``mforacle.c``.
+
+Paper map:
+  * ``svd_compress``      -- Eq. (SVD): SVD of the node-by-time overlap matrix.
+  * ``rbf_fit``           -- Eq. (rbfcoeff) with the side condition P^T a = 0.
+  * ``metric_rotation``   -- Sec. II E: Delta-e = displacement along the metric
+                             eigenvectors, smallest eigenvalue first.
+  * ``Model.loglike``     -- Sec. II E online stage + Eq. (logl_complete).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libmforacle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile mforacle.c with gcc (-O2, OpenMP, strict IEEE: no fast-math)."""
+    src = os.path.join(_HERE, "mforacle.c")
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(src)):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99",
+                           "-D_DEFAULT_SOURCE", "-fno-fast-math", "-ffp-contract=off",
+                           src, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+class _Model(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int), ("P", ctypes.c_int),
+                ("nodes", ctypes.c_void_p), ("W", ctypes.c_void_p), ("eps", ctypes.c_double),
+                ("n_det", ctypes.c_int), ("n_modes", ctypes.c_int), ("rank", ctypes.c_int),
+                ("M", ctypes.c_int), ("ell_m", ctypes.c_void_p), ("basis", ctypes.c_void_p),
+                ("t0", ctypes.c_double), ("dt", ctypes.c_double), ("det", ctypes.c_void_p),
+                ("d_ref", ctypes.c_double), ("R", ctypes.c_void_p), ("centre", ctypes.c_void_p),
+                ("stencil", ctypes.c_int)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build())
+            dp, ip, fp = (ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                          ctypes.POINTER(ctypes.c_float))
+            L.oracle_sylm.argtypes = [ctypes.c_int] * 3 + [ctypes.c_double] * 2 + [dp, dp]
+            L.oracle_spline.argtypes = [ctypes.c_int, dp, ctypes.c_double]
+            L.oracle_spline.restype = ctypes.c_double
+            L.oracle_rbf_eval.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, dp]
+            L.oracle_amplitudes.argtypes = ([ctypes.POINTER(_Model), ctypes.c_int]
+                                            + [ctypes.c_double] * 4 + [dp, dp])
+            L.oracle_loglike.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, fp, fp,
+                                         ctypes.c_int, dp, ctypes.c_int]
+            L.oracle_loglike.restype = ctypes.c_int
+            L.oracle_num_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# ------------------------------------------------------------------ pieces
+def sylm(s: int, l: int, m: int, theta: float, phi: float) -> complex:
+    """Spin-weighted spherical harmonic sY_lm (Eq. h_spherical_harmonic_basis
+    uses s = -2), Wigner-d sum form."""
+    re, im = ctypes.c_double(), ctypes.c_double()
+    lib().oracle_sylm(s, l, m, float(theta), float(phi), ctypes.byref(re), ctypes.byref(im))
+    return complex(re.value, im.value)
+
+
+def spline(y, x: float) -> float:
+    """Not-a-knot cubic spline through y at abscissae 0..n-1, evaluated at x
+    (the online-stage time interpolation, Sec. II E)."""
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    return lib().oracle_spline(len(y), _dp(y), float(x))
+
+
+def svd_compress(Z: np.ndarray, rank: int):
+    """Eq. (SVD): rows of Z [N, M] are node overlap series.  Returns
+    (C [N, rank] complex, B [rank, M] complex, s [min(N,M)]) with
+    Z ~= C @ B, B = first `rank` rows of V^H (orthonormal basis vectors)."""
+    _, s, Vh = np.linalg.svd(Z, full_matrices=False)
+    B = Vh[:rank]
+    C = Z @ B.conj().T
+    return C, B, s
+
+
+def tail_size(tail_degree: int) -> int:
+    """M = C(r + d, r) monomials for degree r in d = 4 (Eq. rbfcoeff)."""
+    return {-1: 0, 0: 1, 1: 5}[tail_degree]
+
+
+def rbf_matrix(X: np.ndarray, Y: np.ndarray, eps: float) -> np.ndarray:
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    return np.exp(-(eps * eps) * d2)
+
+
+def rbf_fit(nodes: np.ndarray, F: np.ndarray, eps: float, tail_degree: int = 1):
+    """Eq. (rbfcoeff): solve [Phi P; P^T 0][a; b] = [F; 0] in FP64 (dense
+    LAPACK solve).  Returns W = [a; b] of shape [N+P, K]."""
+    N = nodes.shape[0]
+    P = tail_size(tail_degree)
+    A = np.zeros((N + P, N + P))
+    A[:N, :N] = rbf_matrix(nodes, nodes, eps)
+    if P:
+        Pm = np.concatenate([np.ones((N, 1)), nodes], axis=1)[:, :P]
+        A[:N, N:] = Pm
+        A[N:, :N] = Pm.T
+    rhs = np.zeros((N + P, F.shape[1]))
+    rhs[:N] = F
+    return np.linalg.solve(A, rhs)
+
+
+def metric_rotation(metric) -> np.ndarray:
+    """Rows = eigenvectors of the metric, ascending eigenvalue (Delta-e_0 along
+    the smallest, Sec. II E); each row's largest-|.| entry made positive."""
+    if metric is None:
+        return np.eye(4)
+    w, V = np.linalg.eigh(np.asarray(metric, dtype=np.float64))
+    R = V[:, np.argsort(w)].T.copy()
+    for i in range(4):
+        if R[i, np.argmax(np.abs(R[i]))] < 0:
+            R[i] = -R[i]
+    return R
+
+
+def pack_node_values(C: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """Column layout of the interpolated quantities.
+    C: [n_det, n_modes, N, rank] complex SVD coefficients;
+    sigma: [n_det, N, n_modes, n_modes] complex Hermitian cross terms.
+    Per (det, mode): rank real parts then rank imaginary parts; then per
+    detector: n_modes real diagonals, Re of the strict upper triangle
+    (row-major), Im of the strict upper triangle."""
+    nd, nm, N, l = C.shape
+    cols = []
+    for k in range(nd):
+        for j in range(nm):
+            cols.append(C[k, j].real)
+            cols.append(C[k, j].imag)
+    iu = np.triu_indices(nm, 1)
+    for k in range(nd):
+        cols.append(np.stack([sigma[k][:, a, a].real for a in range(nm)], axis=1))
+        cols.append(sigma[k][:, iu[0], iu[1]].real)
+        cols.append(sigma[k][:, iu[0], iu[1]].imag)
+    return np.concatenate(cols, axis=1)
+
+
+class Model:
+    """Everything the online stage needs, built in FP64 from an event's node
+    overlaps: per-(det, mode) SVD, one RBF fit for all columns, rotation."""
+
+    def __init__(self, nodes, Z, sigma, rank, eps, tail_degree, modes, det, t0, dt,
+                 d_ref, metric=None, centre=None, stencil=10):
+        nd, nm, N, M = Z.shape
+        self.nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        self.rank, self.eps, self.tail_degree = rank, float(eps), tail_degree
+        self.modes = tuple(tuple(m) for m in modes)
+        self.n_det, self.n_modes, self.M = nd, nm, M
+        C = np.empty((nd, nm, N, rank), complex)
+        B = np.empty((nd, nm, rank, M), complex)
+        self.sv = np.empty((nd, nm, min(N, M)))
+        for k in range(nd):
+            for j in range(nm):
+                C[k, j], B[k, j], self.sv[k, j] = svd_compress(Z[k, j], rank)
+        self.C, self.B = C, B
+        self.F = pack_node_values(C, sigma)
+        self.W = np.ascontiguousarray(rbf_fit(self.nodes, self.F, eps, tail_degree))
+        self.basis = np.ascontiguousarray(np.stack([B.real, B.imag], axis=-1))
+        self.det = np.ascontiguousarray(det, dtype=np.float64)
+        self.t0, self.dt, self.d_ref = float(t0), float(dt), float(d_ref)
+        self.R = np.ascontiguousarray(metric_rotation(metric))
+        self.centre = np.ascontiguousarray(np.zeros(4) if centre is None else centre,
+                                           dtype=np.float64)
+        self.ell_m = np.ascontiguousarray(np.array(self.modes, dtype=np.int32).reshape(-1))
+        self.stencil = stencil
+        self._c = self._struct()
+
+    @classmethod
+    def from_event(cls, ev):
+        from workload.standin import node_overlaps, standin_sigma
+        s = ev.spec
+        return cls(ev.nodes, node_overlaps(ev), standin_sigma(ev, ev.nodes), s.rank, s.eps,
+                   s.tail_degree, s.modes, ev.det, s.t0, s.dt, s.d_ref, ev.metric, ev.centre)
+
+    @property
+    def K(self):
+        return self.F.shape[1]
+
+    @property
+    def N(self):
+        return self.nodes.shape[0]
+
+    def _struct(self):
+        return _Model(self.N, self.K, tail_size(self.tail_degree),
+                      self.nodes.ctypes.data, self.W.ctypes.data, self.eps,
+                      self.n_det, self.n_modes, self.rank, self.M, self.ell_m.ctypes.data,
+                      self.basis.ctypes.data, self.t0, self.dt, self.det.ctypes.data,
+                      self.d_ref, self.R.ctypes.data, self.centre.ctypes.data, self.stencil)
+
+    def rotate(self, theta):
+        return (np.asarray(theta, np.float64) - self.centre) @ self.R.T
+
+    def rbf_eval(self, x):
+        """Interpolated columns at Delta-e points x [Q,4] -> [Q,K]."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        f = np.empty((x.shape[0], self.K))
+        lib().oracle_rbf_eval(ctypes.byref(self._c), x.shape[0], _dp(x), _dp(f))
+        return f
+
+    def amplitudes(self, k, dL, cosi, psi, phic):
+        cr = np.empty(self.n_modes)
+        ci = np.empty(self.n_modes)
+        lib().oracle_amplitudes(ctypes.byref(self._c), k, dL, cosi, psi, phic, _dp(cr), _dp(ci))
+        return cr + 1j * ci
+
+    def loglike(self, intrinsic, extrinsic, nthreads: int = 0):
+        """lnL [Q] (float64) for FP32 inputs intrinsic [Q,4], extrinsic [Q,5];
+        NaN where the spline stencil leaves the sampled window."""
+        th = np.ascontiguousarray(intrinsic, dtype=np.float32)
+        ex = np.ascontiguousarray(extrinsic, dtype=np.float32)
+        out = np.empty(th.shape[0])
+        lib().oracle_loglike(ctypes.byref(self._c), th.shape[0],
+                             th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             ex.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             ex.shape[1], _dp(out), nthreads)
+        return out
+
+
+def num_threads() -> int:
+    return lib().oracle_num_threads()

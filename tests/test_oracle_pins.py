@@ -1,0 +1,324 @@
+"""Pins for the FP64 oracle: each test checks the oracle against something
+other than itself (closed forms, textbook angular dependences, a library
+routine, exact algebraic identities, or the analytic stand-in model)."""
+import numpy as np
+import pytest
+
+from workload import standin
+from workload.standin import make_event, make_queries, spec_for
+
+
+# --------------------------------------------------------------- -2Y_lm
+def test_sylm_closed_form_22(oracle_mod):
+    # -2Y_2,+-2 = sqrt(5/(64 pi)) (1 +- cos i)^2 e^{+-2 i phi}
+    for th in (0.0, 0.3, 1.1, 2.5, np.pi):
+        for ph in (0.0, 0.7, 4.0):
+            ref_p = np.sqrt(5 / (64 * np.pi)) * (1 + np.cos(th)) ** 2 * np.exp(2j * ph)
+            ref_m = np.sqrt(5 / (64 * np.pi)) * (1 - np.cos(th)) ** 2 * np.exp(-2j * ph)
+            assert abs(oracle_mod.sylm(-2, 2, 2, th, ph) - ref_p) < 1e-14
+            assert abs(oracle_mod.sylm(-2, 2, -2, th, ph) - ref_m) < 1e-14
+    # face-on norm |Y22(0)|^2 = 5 / (4 pi)
+    assert abs(abs(oracle_mod.sylm(-2, 2, 2, 0.0, 0.0)) ** 2 - 5 / (4 * np.pi)) < 1e-14
+
+
+def test_sylm_orthonormal_on_sphere(oracle_mod):
+    modes = [(2, 2), (2, -2), (2, 1), (2, -1), (3, 3), (3, -3), (3, 2), (3, -2), (4, 4), (4, -4)]
+    x, wx = np.polynomial.legendre.leggauss(24)     # exact for these band limits
+    nphi = 20
+    phis = 2 * np.pi * np.arange(nphi) / nphi
+    vals = np.array([[[oracle_mod.sylm(-2, l, m, np.arccos(c), p) for p in phis] for c in x]
+                     for (l, m) in modes])
+    w = wx[:, None] * (2 * np.pi / nphi)
+    G = np.einsum("aij,bij,ij->ab", vals, vals.conj(), w)
+    assert np.abs(G - np.eye(len(modes))).max() < 1e-12
+
+
+# ------------------------------------------------- polarisation amplitudes
+@pytest.fixture(scope="module")
+def hm_model(oracle_mod):
+    ev = make_event(spec_for("C1", N=60))
+    m = oracle_mod.Model.from_event(ev)
+    return m
+
+
+def test_mode_polarisation_angular_dependence(hm_model):
+    """c_mu for a detector with F+=1 (resp. Fx=1) must carry the textbook
+    angular dependence of the non-precessing mode polarisations (post-Newtonian
+    mode amplitudes, e.g. Blanchet, Living Rev. Rel. 17, 2 (2014), Sec. 9.5):
+      22: h+ ~ (1+c^2),      hx ~ 2c
+      21: h+ ~ s,            hx ~ s c
+      33: h+ ~ s (1+c^2),    hx ~ 2 s c
+      44: h+ ~ s^2 (1+c^2),  hx ~ 2 s^2 c
+    with hx a quarter cycle behind h+ and the phase e^{-i m phi_c}.  A wrong
+    (-1)^l, a conjugate dropped or m/-m swapped breaks these."""
+    m = hm_model
+    det_save = m.det.copy()
+    m.det[:] = 0.0
+    m.det[0, 0] = 1.0
+    m.det[1, 1] = 1.0
+    m._c = m._struct()
+    try:
+        shapes = {(2, 2): (lambda c, s: 1 + c * c, lambda c, s: 2 * c),
+                  (2, 1): (lambda c, s: s, lambda c, s: s * c),
+                  (3, 3): (lambda c, s: s * (1 + c * c), lambda c, s: 2 * s * c),
+                  (4, 4): (lambda c, s: s * s * (1 + c * c), lambda c, s: 2 * s * s * c)}
+        for j, mode in enumerate(m.modes):
+            fp, fx = shapes[mode]
+            ratios = []
+            for iota in (0.35, 0.9, 1.3, 2.0, 2.7):
+                for phic in (0.2, 2.9):
+                    c, s = np.cos(iota), np.sin(iota)
+                    cp = m.amplitudes(0, 100.0, c, 0.0, phic)[j]
+                    cx = m.amplitudes(1, 100.0, c, 0.0, phic)[j]
+                    ph = np.exp(-1j * mode[1] * phic)
+                    ratios.append((cp / (fp(c, s) * ph), cx / (fx(c, s) * ph)))
+            r = np.array(ratios)
+            assert np.abs(r[:, 0] - r[0, 0]).max() < 1e-12 * abs(r[0, 0])
+            assert np.abs(r[:, 1] - r[0, 1]).max() < 1e-12 * abs(r[0, 1])
+            assert abs(r[0, 0].imag) < 1e-14 and r[0, 0].real > 0
+            # hx lags h+ by a quarter cycle with the stated relative weight
+            assert abs(r[0, 1] - (-1j) * r[0, 0]) < 1e-12
+        # 22 normalisation: |c+| = (D_ref/d_L) sqrt(5/(64 pi)) (1 + cos^2 i)
+        j22 = m.modes.index((2, 2))
+        cp = m.amplitudes(0, 200.0, 0.4, 0.0, 0.0)[j22]
+        assert abs(cp - 0.5 * np.sqrt(5 / (64 * np.pi)) * (1 + 0.16)) < 1e-14
+    finally:
+        m.det[:] = det_save
+        m._c = m._struct()
+
+
+# ------------------------------------------------------------------ spline
+def test_spline_reproduces_cubics(oracle_mod):
+    rng = np.random.default_rng(1)
+    for _ in range(5):
+        p = rng.standard_normal(4)
+        xs = np.arange(10.0)
+        y = np.polyval(p, xs)
+        for x in rng.uniform(0, 9, 7):
+            assert abs(oracle_mod.spline(y, x) - np.polyval(p, x)) < 1e-11 * (1 + abs(np.polyval(p, x)))
+
+
+def test_spline_matches_scipy_not_a_knot(oracle_mod):
+    from scipy.interpolate import CubicSpline
+    rng = np.random.default_rng(2)
+    y = rng.standard_normal(10)
+    cs = CubicSpline(np.arange(10.0), y, bc_type="not-a-knot")
+    for x in np.concatenate([rng.uniform(0, 9, 20), [4.0, 4.5, 5.0]]):
+        assert abs(oracle_mod.spline(y, x) - cs(x)) < 1e-13
+
+
+# --------------------------------------------------------------------- SVD
+def test_svd_eckart_young(oracle_mod):
+    ev = make_event(spec_for("C1", N=300))
+    Z = standin.standin_z(ev, 1, 2, ev.nodes, ev.t_grid)
+    for l in (3, 6, 20):
+        C, B, s = oracle_mod.svd_compress(Z, l)
+        err = np.linalg.norm(Z - C @ B) ** 2
+        assert abs(err - np.sum(s[l:] ** 2)) <= 1e-9 * np.sum(s ** 2)
+        assert np.abs(B @ B.conj().T - np.eye(l)).max() < 1e-12
+
+
+# --------------------------------------------------------------------- RBF
+@pytest.mark.parametrize("cfg,N", [("C0", 200), ("C1", 300)])
+def test_rbf_reproduces_node_values(oracle_mod, cfg, N):
+    ev = make_event(spec_for(cfg, N=N))
+    m = oracle_mod.Model.from_event(ev)
+    f = m.rbf_eval(ev.nodes)
+    assert np.abs(f - m.F).max() <= 1e-10 * np.abs(m.F).max()
+    # side condition P^T a = 0 (standard reading of the garbled condition)
+    Pm = np.concatenate([np.ones((N, 1)), ev.nodes], axis=1)
+    a = m.W[:N]
+    assert np.abs(Pm.T @ a).max() <= 1e-9 * np.abs(a).max()
+
+
+def test_rbf_degree1_tail_reproduces_affine_data(oracle_mod):
+    rng = np.random.default_rng(3)
+    X = standin.ball(rng, 150)
+    A = rng.standard_normal((4, 3))
+    c = rng.standard_normal(3)
+    F = X @ A + c
+    W = oracle_mod.rbf_fit(X, F, 1.5, 1)
+    assert np.abs(W[:150]).max() < 1e-8
+    Xq = standin.ball(rng, 40, r=0.9)
+    Phi = oracle_mod.rbf_matrix(Xq, X, 1.5)
+    fq = Phi @ W[:150] + np.concatenate([np.ones((40, 1)), Xq], 1) @ W[150:]
+    assert np.abs(fq - (Xq @ A + c)).max() < 1e-9
+
+
+def test_metric_rotation_recovers_eigenbasis(oracle_mod):
+    ev = make_event(spec_for("C1", N=20))
+    R = oracle_mod.metric_rotation(ev.metric)
+    assert np.abs(R - ev.R0).max() < 1e-12
+    lam = np.diag(R @ ev.metric @ R.T)
+    assert np.all(np.diff(lam) > 0)
+
+
+# --------------------------------------------------- lnL-level identities
+def _zero_delay_model(oracle_mod, cfg, N):
+    ev = make_event(spec_for(cfg, N=N))
+    ev.det[:, 2] = 0.0
+    return ev, oracle_mod.Model.from_event(ev)
+
+
+def test_lnl_at_node_matches_standin_and_hermitian_unpacking(oracle_mod):
+    """At a node and an exact sample time the interpolants reproduce the
+    stand-in model, so lnL(a) = a X - a^2 Y with X = Re sum conj(c/a) z and
+    Y = 1/2 (c/a)^H Sigma (c/a) from the analytic z, Sigma: pins the SVD
+    reconstruction, the conj placement, the -1/2 factor and the Hermitian
+    rebuild of Sigma from its packed columns (Sigma has Im != 0 here)."""
+    ev, m = _zero_delay_model(oracle_mod, "C1", 300)
+    s = ev.spec
+    rng = np.random.default_rng(5)
+    for idx in rng.choice(s.N, 4, replace=False):
+        y = ev.nodes[idx]
+        theta = (ev.centre + y @ ev.R0).astype(np.float32)
+        y32 = m.rotate(theta[None].astype(np.float64))[0]   # what the oracle sees
+        ext = np.array([[150.0, 0.3, 0.8, 1.9, 0.0]], np.float32)
+        sig = standin.standin_sigma(ev, y32[None])[:, 0]
+        X = Y = 0.0
+        for k in range(s.n_det):
+            c1 = m.amplitudes(k, 100.0, float(ext[0, 1]), float(ext[0, 2]), float(ext[0, 3]))
+            z = np.array([standin.standin_z(ev, k, j, y32[None], np.array([0.0]))[0, 0]
+                          for j in range(s.n_modes)])
+            X += np.real(np.vdot(c1, z))
+            Y += 0.5 * np.real(np.vdot(c1, sig[k] @ c1))
+        a = 100.0 / 150.0
+        got = m.loglike(theta[None], ext)[0]
+        # node reproduction is exact only at the node itself; FP32 rounding of
+        # theta moves the point by ~1e-7, hence the tolerance
+        assert abs(got - (a * X - a * a * Y)) < 2e-4 * (1 + abs(a * X) + abs(a * a * Y))
+
+
+def test_lnl_quadratic_in_amplitude(oracle_mod):
+    ev = make_event(spec_for("C1", N=200))
+    m = oracle_mod.Model.from_event(ev)
+    th, ex = make_queries(ev, 16)
+    d = np.array([100.0, 160.0, 400.0], np.float32)
+    L = []
+    for dl in d:
+        e = ex.copy()
+        e[:, 0] = dl
+        L.append(m.loglike(th, e))
+    a = 100.0 / d.astype(np.float64)
+    # fit aX - a^2 Y from the first two, predict the third
+    X = (L[0] * a[1] ** 2 - L[1] * a[0] ** 2) / (a[0] * a[1] ** 2 - a[1] * a[0] ** 2)
+    Y = (a[0] * X - L[0]) / a[0] ** 2
+    assert np.abs(a[2] * X - a[2] ** 2 * Y - L[2]).max() < 1e-9 * (1 + np.abs(L[2]).max())
+    assert np.all(Y > 0)      # ||h||^2 > 0: Sigma is positive definite
+
+
+def test_lnl_invariances(oracle_mod):
+    ev = make_event(spec_for("C1", N=200))
+    m = oracle_mod.Model.from_event(ev)
+    th, ex = make_queries(ev, 32)
+    base = m.loglike(th, ex)
+    e2 = ex.copy()
+    e2[:, 2] = (ex[:, 2].astype(np.float64) + np.pi).astype(np.float32)
+    # psi -> psi + pi is exact in the antenna patterns (they depend on 2 psi);
+    # FP32 rounding of psi+pi moves psi by <= 2^-22
+    assert np.abs(m.loglike(th, e2) - base).max() < 1e-5 * (1 + np.abs(base).max())
+    ev0 = make_event(spec_for("C0"))
+    m0 = oracle_mod.Model.from_event(ev0)
+    th0, ex0 = make_queries(ev0, 32)
+    b0 = m0.loglike(th0, ex0)
+    e3 = ex0.copy()
+    e3[:, 3] = (ex0[:, 3].astype(np.float64) + np.pi).astype(np.float32)
+    # 22-only: c ~ e^{-2 i phi_c}, so phi_c -> phi_c + pi leaves lnL unchanged
+    assert np.abs(m0.loglike(th0, e3) - b0).max() < 1e-5 * (1 + np.abs(b0).max())
+
+
+def test_max_over_complex_amplitude(oracle_mod):
+    """One detector, one mode: max_c Re(c* z) - |c|^2 sigma / 2 = |z|^2/(2 sigma),
+    reached at c = z / sigma.  (d_L, phi_c) that realise c = z/sigma are
+    computed from the textbook 22 amplitude c = a sqrt(5/64pi)(1+cos^2 i)
+    e^{-2 i phi_c}; z, sigma from the analytic stand-in at a node."""
+    ev = make_event(spec_for("C0"))
+    m = oracle_mod.Model.from_event(ev)
+    y = ev.nodes[17].astype(np.float32)
+    yd = y.astype(np.float64)
+    z = standin.standin_z(ev, 0, 0, yd[None], np.array([0.0]))[0, 0]
+    sig = standin.standin_sigma(ev, yd[None])[0, 0, 0, 0].real
+    cosi = 0.25
+    g = np.sqrt(5 / (64 * np.pi)) * (1 + cosi ** 2)
+    a = abs(z) / sig / g
+    phic = (-np.angle(z) / 2) % np.pi
+    ext = np.array([[100.0 / a, cosi, 0.0, phic, 0.0]], np.float32)
+    best = m.loglike(y[None], ext)[0]
+    assert abs(best - abs(z) ** 2 / (2 * sig)) < 1e-5 * abs(z) ** 2 / (2 * sig)
+    for dd, dp in ((1.02, 0), (0.98, 0), (1, 0.02), (1, -0.02)):
+        e = ext.copy()
+        e[0, 0] *= dd
+        e[0, 3] += dp
+        assert m.loglike(y[None], e)[0] < best
+
+
+def test_rotation_invariance(oracle_mod):
+    """Radial kernel + rotation-closed degree-1 tail: rotating nodes and
+    queries by the same orthogonal matrix leaves lnL unchanged."""
+    ev = make_event(spec_for("C1", N=250))
+    m1 = oracle_mod.Model.from_event(ev)
+    th, ex = make_queries(ev, 24)
+    x = m1.rotate(th)
+    L1 = m1.loglike(th, ex)
+    rng = np.random.default_rng(9)
+    Qr, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    m2 = oracle_mod.Model(ev.nodes @ Qr.T, standin.node_overlaps(ev),
+                          standin.standin_sigma(ev, ev.nodes), ev.spec.rank, ev.spec.eps,
+                          1, ev.spec.modes, ev.det, ev.spec.t0, ev.spec.dt, ev.spec.d_ref)
+    # same query in the rotated frame; FP32 inputs, so compare through
+    # interpolated columns first (FP64 points), then lnL at FP32 level
+    f1 = m1.rbf_eval(x)
+    f2 = m2.rbf_eval(x @ Qr.T)
+    assert np.abs(f1 - f2).max() < 1e-7 * np.abs(f1).max()
+    L2 = m2.loglike((x @ Qr.T).astype(np.float32), ex)
+    assert np.abs(L1 - L2).max() < 5e-3
+
+
+def test_out_of_window_is_nan(oracle_mod):
+    ev = make_event(spec_for("C0"))
+    m = oracle_mod.Model.from_event(ev)
+    th, ex = make_queries(ev, 4)
+    ex[1, 4] = 0.0155          # beyond the +-15.6 ms window minus the stencil
+    ex[2, 4] = -0.0157
+    L = m.loglike(th, ex)
+    assert np.isfinite(L[0]) and np.isnan(L[1]) and np.isnan(L[2]) and np.isfinite(L[3])
+
+
+@pytest.mark.slow
+def test_converges_to_closed_form_as_nodes_grow(oracle_mod):
+    """lnL from the interpolants approaches lnL of the analytic stand-in
+    (continuous t, exact sigma) as N grows at fixed eps = 1.5 (C0 shape)."""
+    errs = []
+    for N in (200, 400, 800, 1600):
+        ev = make_event(spec_for("C0", N=N))
+        m = oracle_mod.Model.from_event(ev)
+        if N == 200:
+            th, ex = make_queries(ev, 200, seed=77)
+        x = m.rotate(th)
+        L = m.loglike(th, ex)
+        ref = np.zeros(len(th))
+        for q in range(len(th)):
+            c = m.amplitudes(0, *map(float, ex[q, :4]))
+            z = standin.standin_z(ev, 0, 0, x[q:q + 1], np.array([float(ex[q, 4])]),
+                                  per_point=True)
+            sg = standin.standin_sigma(ev, x[q:q + 1])[0, 0]
+            ref[q] = np.real(np.vdot(c, z)) - 0.5 * np.real(np.vdot(c, sg @ c))
+        errs.append(np.abs(L - ref).max())
+    assert all(errs[i + 1] < errs[i] for i in range(3)), errs
+    assert errs[-1] < 0.1 * errs[0]
+
+
+def test_face_on_22_is_circular_under_polarisation_angle(hm_model):
+    """Face-on (iota = 0) the 22 signal is circularly polarised: changing psi
+    rotates (F+, Fx), which only shifts the phase of c_22 by 2 psi and leaves
+    |c_22| unchanged, for any detector orientation."""
+    m = hm_model
+    j22 = m.modes.index((2, 2))
+    for k in range(m.n_det):
+        c0 = m.amplitudes(k, 100.0, 1.0, 0.0, 0.3)[j22]
+        for psi in (0.1, 0.7, 1.3, 2.9):
+            c = m.amplitudes(k, 100.0, 1.0, psi, 0.3)[j22]
+            assert abs(abs(c) - abs(c0)) < 1e-14
+            dphi = np.angle(c / c0)
+            assert min(abs(np.exp(1j * dphi) - np.exp(2j * psi)),
+                       abs(np.exp(1j * dphi) - np.exp(-2j * psi))) < 1e-12

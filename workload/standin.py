@@ -1,0 +1,248 @@
+"""Closed-form stand-in workloads (seeded) for configs C0..C4.
+
+Shapes follow the paper's NSBH workloads (Sec. III A: HLV network, modes
+(2,2),(2,1),(3,3),(4,4) of IMRPhenomXHM, 4096 Hz sampling, ~10^3 nodes) with
+the waveform/data inner products replaced by an analytic overlap model:
+
+    z_k,mu(t; y)  = rho_mu * exp(-(t - tau_k,mu . y)^2 / (2 w^2))
+                     * exp(i (phi0_k,mu + beta_k,mu . y + 2 pi f_mu t))
+    sigma_k,mu,nu(y) = s_k rho0^2 amp_mu amp_nu kappa_mu,nu (1 + 0.1 gamma_k . y)
+                       * exp(i (beta_k,mu - beta_k,nu) . y)
+
+with rho_mu = rho0 * amp_mu, f_mu = f22 * m / 2, kappa = 1 on the diagonal and
+0.1 off it (so sigma is Hermitian positive definite for |y| <= 1, as the
+conjugation symmetry of Eq. (conjugation_symmetry) requires).  Nodes y live in
+the metric eigenbasis (Delta-e frame, Sec. II D); queries are drawn there and
+mapped to the sampler frame Theta = c + R0^T x with a seeded orthonormal R0.
+
+Nothing here is the method: the SVD, RBF fit, spline, spherical harmonics and
+lnL combination live in ``oracle/`` (FP64 CPU) and in the CUDA library.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+AMP = {(2, 2): 1.0, (2, 1): 0.3, (3, 3): 0.4, (4, 4): 0.2, (3, 2): 0.25}
+HM4 = ((2, 2), (2, 1), (3, 3), (4, 4))
+
+
+def eps_rule(n_nodes: int) -> float:
+    """Gaussian shape parameter used for C1..C4 (the paper leaves it to the
+    RBF package): eps(N) = 2.0 (N/1500)^0.4, which keeps the FP32 arithmetic
+    error of the interpolant well below |dlnL| = 0.01 while N grows."""
+    return 2.0 * (n_nodes / 1500.0) ** 0.4
+
+
+@dataclasses.dataclass(frozen=True)
+class Spec:
+    name: str
+    n_det: int
+    modes: tuple
+    rank: int
+    M: int
+    N: int
+    Q: int
+    eps: float
+    tail_degree: int = 1
+    rotate: bool = True
+    rho0: float = 20.0
+    width: float = 2e-3
+    f22: float = 100.0
+    dt: float = 1.0 / 4096.0
+    d_ref: float = 100.0
+    det_kind: str = "seeded"   # "optimal" (C0), "seeded" (HLV-like), "et" (C4)
+    seed: int = 0
+
+    @property
+    def n_modes(self) -> int:
+        return len(self.modes)
+
+    @property
+    def K(self) -> int:
+        """Columns interpolated: per (det, mode) Re+Im of `rank` SVD
+        coefficients, then per detector the packed Hermitian sigma block."""
+        return self.n_det * self.n_modes * 2 * self.rank + self.n_det * self.n_modes ** 2
+
+    @property
+    def t0(self) -> float:
+        return -(self.M // 2) * self.dt
+
+
+CONFIGS = {
+    "C0": Spec("C0", 1, ((2, 2),), 8, 128, 200, 1024, 1.5, rotate=False,
+               det_kind="optimal", seed=0),
+    "C1": Spec("C1", 3, HM4, 20, 512, 1500, 65536, eps_rule(1500), seed=1000),
+    "C2": Spec("C2", 3, HM4, 40, 512, 4000, 262144, eps_rule(4000), seed=2000),
+    "C4": Spec("C4", 1, HM4, 80, 2048, 8000, 1000000, eps_rule(8000),
+               det_kind="et", seed=4000),
+}
+
+
+def spec_for(name: str, **over) -> Spec:
+    """A config by name, optionally with fields overridden (e.g. a smaller Q
+    or N for tests)."""
+    s = CONFIGS[name]
+    if over:
+        if "N" in over and "eps" not in over and name != "C0":
+            over["eps"] = eps_rule(over["N"])
+        s = dataclasses.replace(s, **over)
+    return s
+
+
+def c3_specs(n_events: int = 100, seed: int = 3000) -> list:
+    """C3: events with N ~ logU[800,4000], rank ~ U{10..40},
+    Q ~ logU[4096,65536]; modes/detectors as C1."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for e in range(n_events):
+        N = int(round(math.exp(rng.uniform(math.log(800), math.log(4000)))))
+        l = int(rng.integers(10, 41))
+        Q = int(round(math.exp(rng.uniform(math.log(4096), math.log(65536)))))
+        out.append(Spec(f"C3e{e}", 3, HM4, l, 512, N, Q, eps_rule(N), seed=seed + 1 + e))
+    return out
+
+
+def ball(rng, n: int, d: int = 4, r: float = 1.0) -> np.ndarray:
+    """n points uniform in the d-ball of radius r (Gaussian direction,
+    radius r U^(1/d))."""
+    x = rng.standard_normal((n, d))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    return x * (r * rng.random(n) ** (1.0 / d))[:, None]
+
+
+def _unit(rng, d=4):
+    v = rng.standard_normal(d)
+    return v / np.linalg.norm(v)
+
+
+def _canonical_rotation(rng) -> np.ndarray:
+    """Seeded orthonormal 4x4 with each row's largest-|.| entry positive."""
+    q, _ = np.linalg.qr(rng.standard_normal((4, 4)))
+    R = q.T.copy()
+    for i in range(4):
+        if R[i, np.argmax(np.abs(R[i]))] < 0:
+            R[i] = -R[i]
+    return R
+
+
+@dataclasses.dataclass
+class Event:
+    spec: Spec
+    nodes: np.ndarray          # [N,4] float64, Delta-e frame (unit ball)
+    tau: np.ndarray            # [n_det, n_modes, 4] seconds
+    beta: np.ndarray           # [n_det, n_modes, 4] rad
+    phi0: np.ndarray           # [n_det, n_modes]
+    gamma: np.ndarray          # [n_det, 4]
+    s_det: np.ndarray          # [n_det]
+    det: np.ndarray            # [n_det, 3] = (F+0, Fx0, dt_k [s])
+    metric: np.ndarray | None  # [4,4] SPD or None (identity rotation)
+    centre: np.ndarray         # [4]
+    R0: np.ndarray             # [4,4] rows = eigenvectors, ascending eigenvalue
+
+    @property
+    def t_grid(self) -> np.ndarray:
+        s = self.spec
+        return (np.arange(s.M) - s.M // 2) * s.dt
+
+
+def make_event(spec: Spec) -> Event:
+    rng = np.random.default_rng(spec.seed)
+    nodes = ball(rng, spec.N)
+    nd, nm = spec.n_det, spec.n_modes
+    tau = np.empty((nd, nm, 4))
+    beta = np.empty((nd, nm, 4))
+    phi0 = np.empty((nd, nm))
+    for k in range(nd):
+        for j in range(nm):
+            tau[k, j] = 1e-3 * _unit(rng)
+            beta[k, j] = 2.0 * _unit(rng)
+            phi0[k, j] = rng.uniform(0, 2 * np.pi)
+    gamma = np.stack([_unit(rng) for _ in range(nd)])
+    if spec.det_kind == "optimal":
+        s_det = np.ones(nd)
+        det = np.array([[1.0, 0.0, 0.0]])
+    else:
+        s_det = rng.uniform(0.5, 1.5, nd)
+        det = np.empty((nd, 3))
+        for k in range(nd):
+            amp = np.sin(np.pi / 3) if spec.det_kind == "et" else rng.uniform(0.3, 1.0)
+            chi = rng.uniform(0, np.pi)
+            det[k] = (amp * np.cos(2 * chi), amp * np.sin(2 * chi),
+                      0.0 if spec.det_kind == "et" else rng.uniform(-0.021, 0.021))
+        if spec.det_kind == "et":
+            s_det[:] = 1.0
+    if spec.rotate:
+        R0 = _canonical_rotation(rng)
+        lam = np.sort(np.exp(rng.uniform(np.log(0.2), np.log(20.0), 4)))
+        while np.min(np.diff(np.log(lam))) < 0.15:
+            lam = np.sort(np.exp(rng.uniform(np.log(0.2), np.log(20.0), 4)))
+        metric = R0.T @ np.diag(lam) @ R0
+        metric = 0.5 * (metric + metric.T)
+        centre = rng.uniform(-0.5, 0.5, 4)
+    else:
+        R0, metric, centre = np.eye(4), None, np.zeros(4)
+    return Event(spec, nodes, tau, beta, phi0, gamma, s_det, det, metric, centre, R0)
+
+
+def standin_z(ev: Event, k: int, j: int, y: np.ndarray, t: np.ndarray,
+              per_point: bool = False) -> np.ndarray:
+    """Stand-in overlap z_k,mode_j at points y [n,4].  With per_point=False, t
+    is a shared grid [T] and the result is [n,T]; with per_point=True, t is [n]
+    (one time per point) and the result is [n]."""
+    s = ev.spec
+    ell, m = s.modes[j]
+    rho = s.rho0 * AMP[(ell, m)]
+    f = s.f22 * m / 2.0
+    ty = y @ ev.tau[k, j]
+    by = y @ ev.beta[k, j]
+    if not per_point:
+        t, ty, by = t[None, :], ty[:, None], by[:, None]
+    return rho * np.exp(-(t - ty) ** 2 / (2 * s.width ** 2)) * np.exp(
+        1j * (ev.phi0[k, j] + by + 2 * np.pi * f * t))
+
+
+def standin_sigma(ev: Event, y: np.ndarray) -> np.ndarray:
+    """Stand-in cross terms sigma [n_det, n, n_modes, n_modes] (complex)."""
+    s = ev.spec
+    nd, nm = s.n_det, s.n_modes
+    amp = np.array([AMP[md] for md in s.modes])
+    kappa = np.full((nm, nm), 0.1)
+    np.fill_diagonal(kappa, 1.0)
+    out = np.empty((nd, y.shape[0], nm, nm), complex)
+    for k in range(nd):
+        ph = y @ ev.beta[k].T                        # [n, nm]
+        scale = ev.s_det[k] * s.rho0 ** 2 * (1.0 + 0.1 * (y @ ev.gamma[k]))
+        out[k] = (scale[:, None, None] * (amp[:, None] * amp[None, :] * kappa)[None]
+                  * np.exp(1j * (ph[:, :, None] - ph[:, None, :])))
+    return out
+
+
+def node_overlaps(ev: Event) -> np.ndarray:
+    """z at every node on the sample grid: [n_det, n_modes, N, M] complex."""
+    s = ev.spec
+    out = np.empty((s.n_det, s.n_modes, s.N, s.M), complex)
+    for k in range(s.n_det):
+        for j in range(s.n_modes):
+            out[k, j] = standin_z(ev, k, j, ev.nodes, ev.t_grid)
+    return out
+
+
+def make_queries(ev: Event, Q: int, seed: int | None = None, radius: float = 0.9,
+                 tc_range: float = 5e-3):
+    """Q queries: Delta-e points uniform in the ball of radius 0.9, mapped to the
+    sampler frame; extrinsics (d_L, cos iota, psi, phi_c, t_c) drawn as in the
+    paper's prior table restricted to the config ranges.  Returns FP32 arrays
+    intrinsic [Q,4], extrinsic [Q,5] (what both implementations consume)."""
+    rng = np.random.default_rng(ev.spec.seed + 17 if seed is None else seed)
+    x = ball(rng, Q, r=radius)
+    theta = ev.centre[None, :] + x @ ev.R0
+    ext = np.empty((Q, 5))
+    ext[:, 0] = rng.uniform(100.0, 400.0, Q)
+    ext[:, 1] = rng.uniform(-1.0, 1.0, Q)
+    ext[:, 2] = rng.uniform(0.0, np.pi, Q)
+    ext[:, 3] = rng.uniform(0.0, 2 * np.pi, Q)
+    ext[:, 4] = rng.uniform(-tc_range, tc_range, Q)
+    return theta.astype(np.float32), ext.astype(np.float32)
