@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Benchmark: meshfree lnL evaluations per second on GB300.
+
+One step = one mf_loglike call over a batch of Q synthetic sampler points
+(the whole online stage: rotation, RBF + tail, Phi.W contraction, SVD
+reconstruction at each detector delay, extrinsic combination).  Default
+workload: C1 (3 detectors x 4 modes, N = 1500 nodes, rank 20, M = 512,
+Q = 65536 per step).  The line reports the fastest arithmetic form whose lnL
+stays within |dlnL| <= 0.01 of the FP64 oracle on a sample, next to the plain
+FP32 form, the kernel's roofline fraction, an end-to-end number through the C
+ABI with host buffers, and the FP64 CPU oracle timed on this host.
+
+  python bench.py [--gpus N --steps K --warmup W --config C1 --forms fp32,fp16_3term]
+  python bench.py --impl reference ...   # FP64 CPU oracle arm
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "lnL evals/s at |ΔlnL|≤0.01 vs FP64 oracle, chosen vs plain form; % roofline"
+TOL = 0.01
+FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FMA/clk x 2 x max clock
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return d["hbm_gbs"], d["bf16_tflops"], d.get("bf16_tflops_sustained"), "measured"
+    except Exception:
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            self.proc.wait()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic_from_profile(kernel_tag: str, src_files):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken
+    on the current kernel source (sha256 prefix recorded in the summary)."""
+    h = hashlib.sha256()
+    for f in src_files:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    digest = h.hexdigest()[:16]
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    for fn in os.listdir(pdir):
+        txt = open(os.path.join(pdir, fn)).read()
+        m = re.search(rf"traffic\[{re.escape(kernel_tag)}\]\s*=\s*([0-9.eE+]+)\s+bytes/launch\s+src=(\w+)", txt)
+        if m and m.group(2) == digest:
+            return float(m.group(1))
+    return None
+
+
+def build_workload(cfg: str, rank: int):
+    import paper_2508_04172_gb300 as mf
+    from workload import standin
+    from workload.standin import make_event, make_queries, spec_for
+    spec = spec_for(cfg)
+    ev = make_event(spec)
+    m = mf.Interpolant.from_overlaps(ev.nodes, standin.node_overlaps(ev),
+                                     standin.standin_sigma(ev, ev.nodes), spec.rank, spec.eps,
+                                     spec.modes, ev.det, spec.t0, spec.dt, spec.d_ref, ev.metric,
+                                     ev.centre, spec.tail_degree, "fp32")
+    th, ex = make_queries(ev, spec.Q, seed=spec.seed + 17 + 1000 * rank)
+    return spec, ev, m, th, ex
+
+
+def time_form(m, form, d_th, d_ex, d_out, steps, warmup, flush):
+    import torch
+    m.set_form(form)
+    m.set_option("timing", 1)
+    st = torch.cuda.current_stream()
+    for _ in range(warmup):
+        m.loglike(d_th, d_ex, out=d_out)
+    torch.cuda.synchronize()
+    tot, kern = [], []
+    launches = int(m.query("launches"))
+    for _ in range(steps):
+        flush.zero_()                       # evict L2 (256 MB > 129 MB L2), not timed
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        m.loglike(d_th, d_ex, out=d_out)
+        e1.record(st)
+        e1.synchronize()
+        tot.append(e0.elapsed_time(e1))
+        kern.append(m.query("kernel_ms"))
+    m.set_option("timing", 0)
+    return tot, kern, launches * steps
+
+
+def time_e2e(m, form, h_th, h_ex, h_out, steps, warmup, dev):
+    import torch
+    m.set_form(form)
+    Q = h_th.shape[0]
+    d_th = torch.empty_like(h_th, device=dev)
+    d_ex = torch.empty_like(h_ex, device=dev)
+    d_out = torch.empty(Q, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        d_th.copy_(h_th, non_blocking=True)
+        d_ex.copy_(h_ex, non_blocking=True)
+        m.loglike(d_th, d_ex, out=d_out)
+        h_out.copy_(d_out, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        step()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return ms, h_th.numel() * 4 + h_ex.numel() * 4, Q * 4
+
+
+def oracle_baseline(ev, th, ex, budget_s=10.0, cap=None):
+    import oracle
+    om = oracle.Model.from_event(ev)
+    n0 = min(1024, th.shape[0])
+    t = time.perf_counter()
+    om.loglike(th[:n0], ex[:n0])
+    dt = time.perf_counter() - t
+    n = int(min(th.shape[0] if cap is None else cap, max(n0, n0 * budget_s / max(dt, 1e-6))))
+    t = time.perf_counter()
+    ref = om.loglike(th[:n], ex[:n])
+    el = time.perf_counter() - t
+    return om, ref, n, n / el, oracle.num_threads()
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec, ev, m, th, ex = build_workload(args.config, rank)
+    Q = spec.Q
+    d_th = torch.from_numpy(th).to(dev)
+    d_ex = torch.from_numpy(ex).to(dev)
+    d_out = torch.empty(Q, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    # accuracy of each form against the FP64 oracle on a fixed sample
+    import oracle  # noqa: F401  (test infrastructure: accuracy + CPU baseline only)
+    sample = np.random.default_rng(11).choice(Q, min(args.check, Q), replace=False)
+    om = oracle.Model.from_event(ev)
+    ref = om.loglike(th[sample], ex[sample])
+    forms = [f.strip() for f in args.forms.split(",") if f.strip()]
+    res = {}
+    for f in forms:
+        try:
+            m.set_form(f)
+        except Exception as e:  # form not available in this build
+            res[f] = {"error": str(e)}
+            continue
+        out = m.loglike(d_th, d_ex, out=d_out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()[sample].astype(np.float64)
+        err = np.abs(got - ref)
+        res[f] = {"max_abs_dlnl": float(err.max()), "p99_abs_dlnl": float(np.quantile(err, 0.99)),
+                  "median_abs_dlnl": float(np.median(err)), "n_checked": int(len(sample))}
+    # timing
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with clocks:
+        for f in forms:
+            if "error" in res[f]:
+                continue
+            tot, kern, nl = time_form(m, f, d_th, d_ex, d_out, args.steps, args.warmup, flush)
+            res[f].update(ms_per_step=statistics.mean(tot), kernel_ms=statistics.mean(kern),
+                          launches=nl, step_ms_all=tot)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.summary()
+    ok = [f for f in forms if "error" not in res[f] and res[f]["max_abs_dlnl"] <= TOL]
+    plain = "fp32"
+    chosen = min(ok, key=lambda f: res[f]["ms_per_step"]) if ok else plain
+    ms = res[chosen]["ms_per_step"]
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = Q * world / (ms / 1e3)
+
+    # end to end through the C ABI with pinned host buffers
+    h_th = torch.from_numpy(th).pin_memory()
+    h_ex = torch.from_numpy(ex).pin_memory()
+    h_out = torch.empty(Q, dtype=torch.float32).pin_memory()
+    e2e_ms, bi, bo = time_e2e(m, chosen, h_th, h_ex, h_out, args.steps, args.warmup, dev)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # roofline of the dominant kernel (the fused lnL kernel of the chosen form)
+    hbm, bf16, bf16s, src = _peaks()
+    N, K, P = spec.N, spec.K, 5 if spec.tail_degree == 1 else (1 if spec.tail_degree == 0 else 0)
+    flops = 2.0 * Q * (N + P) * K
+    kms = res[chosen]["kernel_ms"]
+    if chosen == "fp32":
+        roof = {"bound": "alu", "peak": round(FP32_SIMT_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (derived)"}
+        tag, srcs = "fp32_kernel", ["paper_2508_04172_gb300/csrc/mf_fp32.cu",
+                                    "paper_2508_04172_gb300/csrc/mf_epilogue.cuh"]
+    else:
+        roof = {"bound": "tensor", "peak": bf16, "unit": "TFLOP/s",
+                "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate)"}
+        tag, srcs = "tc_kernel", ["paper_2508_04172_gb300/csrc/mf_tc.cu",
+                                  "paper_2508_04172_gb300/csrc/mf_epilogue.cuh"]
+    achieved = flops / (kms / 1e3) / 1e12
+    roof.update(achieved=round(achieved, 2), frac=round(achieved / roof["peak"], 4),
+                traffic=_traffic_from_profile(tag, srcs), kernel=tag,
+                algorithmic_flops_per_launch=flops, kernel_ms=round(kms, 4))
+
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "fp16_3term": "f16x3", "bf16_3term": "bf16x3",
+                      "fp16": "f16", "bf16": "bf16", "fp16_wsplit": "f16x2",
+                      "bf16_wsplit": "bf16x2"}.get(chosen, chosen),
+            "data": "synthetic (seeded closed-form stand-in overlaps)",
+            "config": {"workload": f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, "
+                                   f"N={spec.N}+{P} nodes, rank {spec.rank}, M={spec.M}, "
+                                   f"K={K}, Q={Q} per step per GPU",
+                       "form": chosen, "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": round(Q * world / (e2e_ms / 1e3), 1), "unit": "evals/s",
+                    "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+                    "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": int(res[chosen]["launches"]),
+            "clocks": ck,
+            "accuracy": {f: {k: v for k, v in r.items() if k.endswith("dlnl") or k == "n_checked"}
+                         for f, r in res.items() if "error" not in r},
+            "forms": {f: {"ms_per_step": round(r["ms_per_step"], 4),
+                          "evals_per_s": round(Q * world / (r["ms_per_step"] / 1e3), 1),
+                          "within_tol": r["max_abs_dlnl"] <= TOL}
+                      for f, r in res.items() if "error" not in r},
+            "speedup_vs_plain_fp32": (round(res[plain]["ms_per_step"] / ms, 3)
+                                      if plain in res and "error" not in res[plain] else None)}
+    # CPU FP64 oracle on this host (rank 0, N = 1 only)
+    if rank == 0 and world == 1:
+        _, _, n, rate, cores = oracle_baseline(ev, th, ex, budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": round(rate, 1), "unit": "evals/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"first {n} queries of the {spec.name} batch, FP64 C "
+                                          f"+ OpenMP, interpolants built beforehand"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    from workload.standin import make_event, make_queries, spec_for
+    spec = spec_for(args.config)
+    ev = make_event(spec)
+    om = oracle.Model.from_event(ev)
+    th, ex = make_queries(ev, spec.Q, seed=spec.seed + 17)
+    n0 = 512
+    t = time.perf_counter()
+    om.loglike(th[:n0], ex[:n0])
+    per = (time.perf_counter() - t) / n0
+    budget = 150.0 / max(1, args.steps + args.warmup)        # whole run within a few minutes
+    n = int(max(256, min(spec.Q, budget / max(per, 1e-9))))
+    for i in range(args.warmup):
+        om.loglike(th[:n], ex[:n])
+    ts = []
+    for i in range(args.steps):
+        s = (i * n) % max(1, spec.Q - n)
+        t = time.perf_counter()
+        om.loglike(th[s:s + n], ex[s:s + n])
+        ts.append(time.perf_counter() - t)
+    ms = 1e3 * statistics.mean(ts)
+    v = n / (ms / 1e3)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "evals/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded closed-form stand-in overlaps)",
+            "config": {"workload": f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, "
+                                   f"N={spec.N} nodes, rank {spec.rank}, M={spec.M}, K={spec.K}",
+                       "form": "fp64 CPU oracle", "parallelism": "host cores"},
+            "cpu_baseline": {"value": round(v, 1), "unit": "evals/s", "cores": oracle.num_threads(),
+                             "kind": "oracle",
+                             "sample": f"{n} queries per step of the {spec.name} batch"},
+            "e2e": {"value": round(v, 1), "unit": "evals/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="C1", choices=["C0", "C1", "C2", "C4"])
+    ap.add_argument("--forms", default="fp32,fp16_3term,bf16_3term,fp16_wsplit,fp16,bf16")
+    ap.add_argument("--check", type=int, default=2048, help="queries checked against the oracle")
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        import paper_2508_04172_gb300 as mf
+        mf.build()
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * mf.h -- C ABI of the GB300 meshfree log-likelihood library (libmf.so).
+ *
+ * The library evaluates the online stage of the meshfree likelihood
+ * interpolation of Sec. II E for large batches of sampler points: rotate the
+ * intrinsic point into the metric eigenbasis, evaluate the Gaussian RBF
+ * interpolants with their polynomial tail (Eq. rbfcoeff) for every SVD
+ * coefficient of every mode/detector overlap series and for the mode cross
+ * terms, rebuild each detector's overlap at its delay with a cubic spline
+ * through 10 samples (Eq. SVD + Sec. II E), and combine them with the
+ * extrinsic amplitudes into lnL (Eqs. logl_basic, projected_h_fd,
+ * hplus_hcross_decomposed1/2, logl_complete).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: MF_OK (0) or a negative MF_E_* code; mf_error_string()
+ *     names it.  Nothing aborts the process.
+ *   - Host inputs (const double* / const int*) are copied before return; the
+ *     caller keeps ownership.  Device pointers (mf_loglike*) are borrowed for
+ *     the duration of the asynchronous call; the caller keeps them alive until
+ *     the stream has passed the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - The handle owns all device memory it allocates; mf_free releases it.
+ *   - All work runs on the GPU.  There is no CPU fallback: without a CUDA
+ *     device the calls return MF_E_CUDA.
+ *   - A handle is not thread-safe: calls on one handle must be serialised by
+ *     the caller (different handles are independent).
+ */
+#ifndef MF_H
+#define MF_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define MF_API __attribute__((visibility("default")))
+#else
+#define MF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mf_handle mf_handle;
+
+enum {
+    MF_OK = 0,
+    MF_E_INVAL = -1,    /* bad argument (NULL, size out of range, wrong order) */
+    MF_E_NOMEM = -2,    /* device or host allocation failed                    */
+    MF_E_CUDA = -3,     /* a CUDA runtime / library call failed                */
+    MF_E_ILLCOND = -4,  /* RBF system not positive definite / too ill-conditioned */
+    MF_E_RANGE = -5,    /* some queries left the sampled time window (their lnL = NaN) */
+    MF_E_TIMEOUT = -6,  /* a bounded device-side wait gave up                  */
+    MF_E_NOTIMPL = -7,  /* option not implemented                              */
+    MF_E_STATE = -8     /* handle not fully configured for this call           */
+};
+
+/* Radial kernel of Eq. (rbfcoeff).  Gaussian phi(r) = exp(-(eps r)^2). */
+typedef enum { MF_RBF_GAUSSIAN = 0 } mf_rbf;
+
+/* Arithmetic of the Phi.W contraction (the interpolant evaluation).
+ *   FP32        : FP32 SIMT FMAs (the plain form).
+ *   BF16/FP16   : one tcgen05 MMA with 16-bit Phi and W, FP32 accumulation.
+ *   *_WSPLIT    : Phi.W_hi + Phi.W_lo (W split into two 16-bit parts).
+ *   *_3TERM     : Phi_hi.W_hi + Phi_hi.W_lo + Phi_lo.W_hi.
+ * FP16 forms scale Phi by 2^14 and each W column by a power of two so that
+ * both stay in the normal FP16 range; the scale is undone in FP32. */
+typedef enum {
+    MF_FORM_FP32 = 0,
+    MF_FORM_BF16 = 1,
+    MF_FORM_FP16 = 2,
+    MF_FORM_BF16_WSPLIT = 3,
+    MF_FORM_FP16_WSPLIT = 4,
+    MF_FORM_BF16_3TERM = 5,
+    MF_FORM_FP16_3TERM = 6
+} mf_form;
+
+/* Name of a status code (static string). */
+MF_API const char *mf_error_string(int status);
+
+/* Library version string, e.g. "mf 0.1 sm_103a". */
+MF_API const char *mf_version(void);
+
+/*
+ * SVD compression of one overlap matrix (Eq. SVD).
+ *   z      : host, [N][M][2] FP64 (re, im) -- row n = overlap series at node n.
+ *   coef   : host out, [N][rank][2]  -- C_{n,i} = sum_t z_n(t) conj(u_i(t)).
+ *   basis  : host out, [rank][M][2]  -- orthonormal u_i (rows of V^H),
+ *            ordered by decreasing singular value.
+ *   sv     : host out or NULL, [rank] singular values.
+ * Runs on the GPU in FP64 (dense SVD, then projection C = Z V).  Synchronous.
+ * Requires N >= M (at least as many nodes as time samples),
+ * 1 <= rank <= M <= 8192.
+ */
+MF_API int mf_svd_compress(const double *z, int N, int M, int rank, double *coef, double *basis,
+                    double *sv, void *stream);
+
+/*
+ * Build the interpolants (Eq. rbfcoeff) for K columns at N nodes.
+ *   nodes       : host [N][4] FP64, node coordinates in the metric eigenbasis.
+ *   node_values : host [N][K] FP64, the quantities interpolated: per
+ *                 (detector, mode) the rank real parts then rank imaginary
+ *                 parts of the SVD coefficients; then per detector the cross
+ *                 terms sigma: n_modes real diagonals, Re of the strict upper
+ *                 triangle (row-major), Im of the strict upper triangle.
+ *   rbf, eps    : radial kernel and shape parameter (eps > 0).
+ *   tail_degree : -1 (none), 0 (constant) or 1 (affine: 1, x1..x4).
+ * Solves [Phi P; P^T 0][a; b] = [F; 0] on the GPU in FP64 (Cholesky of Phi
+ * plus the tail Schur complement) and estimates cond(Phi).  Returns
+ * MF_E_ILLCOND if Phi is not numerically positive definite.  Synchronous on
+ * `stream`.  Limits: 1 <= N <= 65536, 1 <= K <= 4096.
+ */
+MF_API int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rbf rbf,
+             double eps, int tail_degree, void *stream, mf_handle **out);
+
+/*
+ * Column layout of the handle's K columns (must match node_values above):
+ * n_det detectors, n_modes modes with (l, m) pairs in ell_m [n_modes][2]
+ * (m > 0; the negative-m mode h_{l,-m} is the one interpolated, Eqs.
+ * hplus_hcross_decomposed1/2), `rank` SVD coefficients per mode.  Requires
+ * K == n_det*n_modes*2*rank + n_det*n_modes^2.  Supported modes: (2,2),
+ * (2,1), (3,3), (3,2), (4,4); n_modes <= 5; n_det <= 8; rank <= 128.
+ */
+MF_API int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m, int rank);
+
+/*
+ * SVD basis vectors of every (detector, mode) overlap series (Eq. SVD).
+ *   basis : host [n_det][n_modes][rank][M][2] FP64 (re, im).
+ *   t0, dt: time of sample 0 and the sample spacing (seconds).
+ * The series is evaluated at t = t_c + dt_k with a not-a-knot cubic spline
+ * through the 10 samples j-4..j+5, j = floor((t - t0)/dt) (Sec. II E).
+ */
+MF_API int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, double dt);
+
+/*
+ * Frozen antenna patterns and delays (Eq. projected_h_fd):
+ *   det : host [n_det][3] = F+(psi=0), Fx(psi=0), dt_k (seconds from
+ *         geocentre); F+(psi) = F+0 cos2psi + Fx0 sin2psi,
+ *         Fx(psi) = -F+0 sin2psi + Fx0 cos2psi.
+ *   d_ref: luminosity distance at which the node overlaps were computed;
+ *         the amplitude of a query is d_ref / d_L.
+ */
+MF_API int mf_set_detectors(mf_handle *h, const double *det, double d_ref);
+
+/*
+ * Sampler frame -> metric eigenbasis (Sec. II E, Delta-e coordinates):
+ * x = R (theta - centre), R = rows of metric eigenvectors by ascending
+ * eigenvalue, each row's largest-|.| entry positive.  metric: host [4][4]
+ * symmetric positive definite, or NULL for R = I.  centre: host [4] or NULL
+ * for 0.  The 4x4 eigendecomposition runs on the GPU (FP64 Jacobi).
+ */
+MF_API int mf_set_rotation(mf_handle *h, const double *metric, const double *centre);
+
+/* Select the Phi.W arithmetic (default MF_FORM_FP32).  Converts the weights
+ * for the form on first use (synchronous on the legacy stream). */
+MF_API int mf_set_form(mf_handle *h, mf_form form);
+
+/*
+ * lnL for Q queries, asynchronous on `stream` (Eq. logl_complete read with
+ * the -1/2 ||h||^2 of Eq. logl_basic):
+ *   lnL_q = sum_k [ Re sum_mu conj(c_k,mu) z_k,mu(t_c + dt_k)
+ *                   - 1/2 sum_mu,nu conj(c_k,mu) sigma_k,mu,nu c_k,nu ],
+ *   c_k,mu = (d_ref/d_L) 1/2 [ (F+ + i Fx) Y_{l,-m} + (-1)^l (F+ - i Fx) conj(Y_{l,m}) ],
+ *   Y = -2Y_lm(iota, phi_c).
+ * intrinsic : device [Q][4] FP32, sampler-frame coordinates.
+ * extrinsic : device [Q][E] FP32, E >= 5, columns (d_L [Mpc], cos iota,
+ *             psi, phi_c, t_c [s]).
+ * out_lnL   : device [Q] FP32, written by the call.
+ * Queries whose spline stencil leaves the sampled window get NaN and are
+ * counted; mf_sync_status() reports them.  Q == 0 is a no-op.  Q <= 2^26.
+ */
+MF_API int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int Q, int E,
+               float *out_lnL, void *stream);
+
+/*
+ * Interpolated columns only (the Phi.W stage, Eq. rbfcoeff), in the
+ * node_values column order: out [Q][K] device FP32.  Asynchronous.
+ */
+MF_API int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *out, void *stream);
+
+/* Tuning / instrumentation knobs (host-side, take effect at the next call):
+ *   "timing"   : 1 = record CUDA events around the main lnL kernel of each
+ *                mf_loglike (read back with mf_query "kernel_ms"), 0 = off.
+ *   "pass_max" : widest column pass (16..512, multiple of 16) the tcgen05
+ *                forms may use; re-lays out the weights.
+ *   "tc_ctas_per_sm" : persistent CTAs per SM for the tcgen05 forms (1..2). */
+MF_API int mf_set_option(mf_handle *h, const char *key, double value);
+
+/* Wait for `stream`, then report device-side status accumulated since the
+ * last call: MF_OK, or MF_E_RANGE with *n_bad (if non-NULL) = number of
+ * out-of-window queries.  Resets the counter. */
+MF_API int mf_sync_status(mf_handle *h, void *stream, long long *n_bad);
+
+/* Scalar diagnostics: "cond" (2-norm condition estimate of Phi), "lambda_min",
+ * "lambda_max", "cancel" (max over sampled nodes/columns of sum_n |a_n phi_n|
+ * / max |F|), "N", "K", "Kdev" (padded device columns), "n_pass" (column
+ * passes of the current form), "form", "launches" (kernel launches per
+ * mf_loglike), "kernel_ms" (main-kernel time of the last mf_loglike when the
+ * "timing" option is on; waits for that kernel). */
+MF_API int mf_query(const mf_handle *h, const char *key, double *value);
+
+/* Copy the FP64 weights [(N+P)][K] (a rows, then tail b rows) to host. */
+MF_API int mf_get_weights(const mf_handle *h, double *W_host, size_t count);
+
+MF_API void mf_free(mf_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MF_H */

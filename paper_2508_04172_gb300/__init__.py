@@ -1,0 +1,237 @@
+"""GB300 meshfree log-likelihood library: Python binding of libmf.so.
+
+Thin ctypes marshalling over the C ABI declared in ``include/mf.h`` (same
+names).  Every computation runs in the library's CUDA kernels; PyTorch is only
+used to hand over device buffers and streams.  There is no CPU path: if the
+shared library has not been built, or no GPU is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import SO as _SO_PATH, build
+
+__all__ = ["build", "lib", "MFError", "Interpolant", "svd_compress", "FORMS",
+           "pack_node_values"]
+
+MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
+MF_E_ILLCOND, MF_E_RANGE, MF_E_TIMEOUT, MF_E_NOTIMPL, MF_E_STATE = -4, -5, -6, -7, -8
+FORMS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16_wsplit": 3, "fp16_wsplit": 4,
+         "bf16_3term": 5, "fp16_3term": 6}
+
+_lib = None
+
+
+class MFError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {lib().mf_error_string(code).decode()} ({code})")
+
+
+def lib():
+    """The loaded libmf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_SO_PATH):
+            raise RuntimeError(f"libmf.so not built ({_SO_PATH}); run "
+                               "paper_2508_04172_gb300.build()")
+        L = ctypes.CDLL(_SO_PATH)
+        vp, ip, dp, fp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_float
+        L.mf_error_string.restype = ctypes.c_char_p
+        L.mf_error_string.argtypes = [ip]
+        L.mf_version.restype = ctypes.c_char_p
+        L.mf_svd_compress.argtypes = [vp, ip, ip, ip, vp, vp, vp, vp]
+        L.mf_build.argtypes = [vp, vp, ip, ip, ip, dp, ip, vp, ctypes.POINTER(vp)]
+        L.mf_set_layout.argtypes = [vp, ip, ip, vp, ip]
+        L.mf_set_basis.argtypes = [vp, vp, ip, dp, dp]
+        L.mf_set_detectors.argtypes = [vp, vp, dp]
+        L.mf_set_rotation.argtypes = [vp, vp, vp]
+        L.mf_set_form.argtypes = [vp, ip]
+        L.mf_loglike.argtypes = [vp, vp, vp, ip, ip, vp, vp]
+        L.mf_eval_columns.argtypes = [vp, vp, ip, vp, vp]
+        L.mf_sync_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.mf_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
+        L.mf_get_weights.argtypes = [vp, vp, ctypes.c_size_t]
+        L.mf_set_option.argtypes = [vp, ctypes.c_char_p, dp]
+        L.mf_free.argtypes = [vp]
+        L.mf_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, what: str):
+    if rc != MF_OK:
+        raise MFError(rc, what)
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def svd_compress(Z: np.ndarray, rank: int, stream=None):
+    """mf_svd_compress: Z [N, M] complex -> (coef [N, rank], basis [rank, M], sv)."""
+    Z = np.ascontiguousarray(Z, dtype=np.complex128)
+    N, M = Z.shape
+    coef = np.empty((N, rank), np.complex128)
+    basis = np.empty((rank, M), np.complex128)
+    sv = np.empty(rank)
+    _check(lib().mf_svd_compress(_ptr(Z), N, M, rank, _ptr(coef), _ptr(basis), _ptr(sv),
+                                 _stream_ptr(stream) if stream is not None else None),
+           "mf_svd_compress")
+    return coef, basis, sv
+
+
+def pack_node_values(coef: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """Arrange SVD coefficients [n_det, n_modes, N, rank] (complex) and cross
+    terms [n_det, N, n_modes, n_modes] (complex Hermitian) into the [N, K]
+    node_values layout mf_build documents."""
+    nd, nm, N, l = coef.shape
+    K = nd * nm * 2 * l + nd * nm * nm
+    out = np.empty((N, K))
+    c = 0
+    for k in range(nd):
+        for j in range(nm):
+            out[:, c:c + l] = coef[k, j].real
+            out[:, c + l:c + 2 * l] = coef[k, j].imag
+            c += 2 * l
+    rows, cols = np.triu_indices(nm, 1)
+    for k in range(nd):
+        for a in range(nm):
+            out[:, c + a] = sigma[k, :, a, a].real
+        c += nm
+        out[:, c:c + len(rows)] = sigma[k][:, rows, cols].real
+        c += len(rows)
+        out[:, c:c + len(rows)] = sigma[k][:, rows, cols].imag
+        c += len(rows)
+    return out
+
+
+class Interpolant:
+    """Owns an mf_handle: interpolants built on the GPU plus layout, basis,
+    detectors, rotation and the selected arithmetic form."""
+
+    def __init__(self, nodes, node_values, eps, tail_degree=1, stream=None):
+        nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+        F = np.ascontiguousarray(node_values, dtype=np.float64)
+        self.N, self.K = F.shape
+        self.tail_degree = int(tail_degree)
+        h = ctypes.c_void_p()
+        _check(lib().mf_build(_ptr(nodes), _ptr(F), self.N, self.K, 0, float(eps),
+                              int(tail_degree), _stream_ptr(stream) if stream is not None else None,
+                              ctypes.byref(h)), "mf_build")
+        self._h = h
+
+    @classmethod
+    def from_overlaps(cls, nodes, Z, sigma, rank, eps, modes, det, t0, dt, d_ref,
+                      metric=None, centre=None, tail_degree=1, form="fp32"):
+        """Full start-up on the GPU from node overlaps Z [n_det, n_modes, N, M]
+        (complex) and cross terms sigma [n_det, N, n_modes, n_modes]."""
+        nd, nm, N, M = Z.shape
+        coef = np.empty((nd, nm, N, rank), np.complex128)
+        basis = np.empty((nd, nm, rank, M), np.complex128)
+        for k in range(nd):
+            for j in range(nm):
+                coef[k, j], basis[k, j], _ = svd_compress(Z[k, j], rank)
+        self = cls(nodes, pack_node_values(coef, sigma), eps, tail_degree)
+        self.set_layout(nd, nm, modes, rank)
+        self.set_basis(basis, t0, dt)
+        self.set_detectors(det, d_ref)
+        self.set_rotation(metric, centre)
+        self.set_form(form)
+        return self
+
+    def set_layout(self, n_det, n_modes, modes, rank):
+        em = np.ascontiguousarray(np.array(modes, dtype=np.int32).reshape(-1))
+        _check(lib().mf_set_layout(self._h, n_det, n_modes, _ptr(em), rank), "mf_set_layout")
+        self.n_det, self.n_modes, self.rank = n_det, n_modes, rank
+
+    def set_basis(self, basis, t0, dt):
+        b = np.ascontiguousarray(np.stack([np.real(basis), np.imag(basis)], -1), dtype=np.float64)
+        _check(lib().mf_set_basis(self._h, _ptr(b), b.shape[-2], float(t0), float(dt)),
+               "mf_set_basis")
+
+    def set_detectors(self, det, d_ref):
+        d = np.ascontiguousarray(det, dtype=np.float64)
+        _check(lib().mf_set_detectors(self._h, _ptr(d), float(d_ref)), "mf_set_detectors")
+
+    def set_rotation(self, metric=None, centre=None):
+        m = None if metric is None else np.ascontiguousarray(metric, dtype=np.float64)
+        c = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
+        _check(lib().mf_set_rotation(self._h, None if m is None else _ptr(m),
+                                     None if c is None else _ptr(c)), "mf_set_rotation")
+
+    def set_form(self, form):
+        f = FORMS[form] if isinstance(form, str) else int(form)
+        _check(lib().mf_set_form(self._h, f), "mf_set_form")
+
+    def loglike(self, intrinsic, extrinsic, out=None, stream=None):
+        """lnL for device tensors intrinsic [Q,4] and extrinsic [Q,E] (FP32,
+        contiguous, CUDA); returns (or fills) out [Q] FP32."""
+        import torch
+        assert intrinsic.is_cuda and intrinsic.dtype == torch.float32 and intrinsic.is_contiguous()
+        assert extrinsic.is_cuda and extrinsic.dtype == torch.float32 and extrinsic.is_contiguous()
+        Q, E = extrinsic.shape
+        if out is None:
+            out = torch.empty(Q, dtype=torch.float32, device=intrinsic.device)
+        _check(lib().mf_loglike(self._h, ctypes.c_void_p(intrinsic.data_ptr()),
+                                ctypes.c_void_p(extrinsic.data_ptr()), Q, E,
+                                ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+               "mf_loglike")
+        return out
+
+    def eval_columns(self, intrinsic, out=None, stream=None):
+        import torch
+        Q = intrinsic.shape[0]
+        if out is None:
+            out = torch.empty((Q, self.K), dtype=torch.float32, device=intrinsic.device)
+        _check(lib().mf_eval_columns(self._h, ctypes.c_void_p(intrinsic.data_ptr()), Q,
+                                     ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+               "mf_eval_columns")
+        return out
+
+    def sync_status(self, stream=None):
+        """(status, n_bad): waits for the stream; MF_E_RANGE if queries left
+        the sampled time window since the last call."""
+        n = ctypes.c_longlong()
+        rc = lib().mf_sync_status(self._h, _stream_ptr(stream), ctypes.byref(n))
+        if rc not in (MF_OK, MF_E_RANGE):
+            raise MFError(rc, "mf_sync_status")
+        return rc, n.value
+
+    def set_option(self, key, value):
+        _check(lib().mf_set_option(self._h, key.encode(), float(value)), f"mf_set_option({key})")
+
+    def query(self, key):
+        v = ctypes.c_double()
+        _check(lib().mf_query(self._h, key.encode(), ctypes.byref(v)), f"mf_query({key})")
+        return v.value
+
+    def weights(self):
+        """FP64 weights [(N+P), K]: RBF coefficients a, then tail b."""
+        rows = self.N + {1: 5, 0: 1, -1: 0}[self.tail_degree]
+        buf = np.empty((rows, self.K))
+        _check(lib().mf_get_weights(self._h, _ptr(buf), buf.size), "mf_get_weights")
+        return buf
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mf_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

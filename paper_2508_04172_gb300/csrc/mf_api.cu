@@ -1,0 +1,467 @@
+// C ABI of libmf: handle management, configuration, device column layout,
+// weight conversion for each arithmetic form and the lnL launch.
+#include "mf_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+namespace mf {
+int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st);
+int metric_eig(const double *metric, double *R_out);
+int svd_compress(const double *z, int N, int M, int rank, double *coef, double *basis, double *sv,
+                 cudaStream_t st);
+int convert_tc_weights(mf_handle *h, mf_form f);
+}  // namespace mf
+
+namespace {
+
+bool supported_mode(int l, int m) {
+    return (l == 2 && (m == 2 || m == 1)) || (l == 3 && (m == 3 || m == 2)) || (l == 4 && m == 4);
+}
+
+bool is_tc_form(mf_form f) { return f != MF_FORM_FP32; }
+
+__global__ void convert_fp32_kernel(const double *__restrict__ W64, int rows, int K,
+                                    const int *__restrict__ user_of_dev, int Kdev, int Nk,
+                                    float *__restrict__ W32) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = blockIdx.y;
+    if (c >= Kdev) return;
+    int u = user_of_dev[c];
+    float v = 0.f;
+    if (u >= 0 && n < rows) v = (float)W64[(size_t)n * K + u];
+    W32[(size_t)n * Kdev + c] = v;
+}
+
+__global__ void prescale_nodes(const double *__restrict__ y, int N, int Nk, double pre,
+                               float4 *__restrict__ out) {
+    int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Nk) return;
+    if (n < N)
+        out[n] = make_float4((float)(pre * y[4 * n]), (float)(pre * y[4 * n + 1]),
+                             (float)(pre * y[4 * n + 2]), (float)(pre * y[4 * n + 3]));
+    else
+        out[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+void free_form(mf_handle *h) {
+    if (h->d_W32) cudaFree(h->d_W32);
+    if (h->d_Whi) cudaFree(h->d_Whi);
+    if (h->d_Wlo) cudaFree(h->d_Wlo);
+    if (h->d_colscale) cudaFree(h->d_colscale);
+    if (h->d_user_of_dev) cudaFree(h->d_user_of_dev);
+    h->d_W32 = nullptr;
+    h->d_Whi = h->d_Wlo = nullptr;
+    h->d_colscale = nullptr;
+    h->d_user_of_dev = nullptr;
+}
+
+}  // namespace
+
+namespace mf {
+
+// Device column layout: per detector, its overlap groups (interleaved Re/Im
+// of the rank coefficients, padded to 8) then its cross-term group; groups
+// are packed into passes of at most pass_max columns (each padded to 16).
+int build_layout(mf_handle *h) {
+    const int nd = h->n_det, nm = h->n_modes, l = h->rank;
+    auto up = [](int x, int a) { return (x + a - 1) / a * a; };
+    struct G { int kind, det, mode, width; };
+    std::vector<G> gs;
+    for (int k = 0; k < nd; ++k) {
+        for (int mu = 0; mu < nm; ++mu) gs.push_back({0, k, mu, up(2 * l, kGroupAlign)});
+        gs.push_back({1, k, 0, up(nm * nm, kGroupAlign)});
+    }
+    if ((int)gs.size() > kMaxGroups) return MF_E_INVAL;
+    int total = 0, gmax = 0;
+    for (auto &g : gs) { total += g.width; gmax = std::max(gmax, g.width); }
+    const int pmax = std::max(h->pass_max, up(gmax, kPassAlign));
+    const int npass_min = (total + pmax - 1) / pmax;
+    const int target = (total + npass_min - 1) / npass_min;
+    h->groups.clear();
+    h->passes.clear();
+    Pass cur{0, 0, 0, 0};
+    int col = 0;
+    for (size_t i = 0; i < gs.size(); ++i) {
+        if (cur.ng > 0 && (cur.width + gs[i].width > pmax || cur.width >= target)) {
+            cur.width = up(cur.width, kPassAlign);
+            h->passes.push_back(cur);
+            col += cur.width;
+            cur = Pass{col, 0, (int)h->groups.size(), 0};
+        }
+        Group g{gs[i].kind, gs[i].det, gs[i].mode, cur.width, gs[i].width};
+        h->groups.push_back(g);
+        cur.width += gs[i].width;
+        cur.ng++;
+    }
+    cur.width = up(cur.width, kPassAlign);
+    h->passes.push_back(cur);
+    col += cur.width;
+    if ((int)h->passes.size() > kMaxPass) return MF_E_INVAL;
+    h->Kdev = col;
+    // device column -> user column (node_values order)
+    h->user_of_dev.assign(h->Kdev, -1);
+    const int sig0 = nd * nm * 2 * l;
+    const int nup = nm * (nm - 1) / 2;
+    for (auto &ps : h->passes)
+        for (int gi = ps.g0; gi < ps.g0 + ps.ng; ++gi) {
+            const Group &g = h->groups[gi];
+            int base = ps.col0 + g.col;
+            if (g.kind == 0) {
+                int ucol = (g.det * nm + g.mode) * 2 * l;
+                for (int i = 0; i < l; ++i) {
+                    h->user_of_dev[base + 2 * i] = ucol + i;
+                    h->user_of_dev[base + 2 * i + 1] = ucol + l + i;
+                }
+            } else {
+                int ucol = sig0 + g.det * nm * nm;
+                for (int a = 0; a < nm; ++a) h->user_of_dev[base + a] = ucol + a;
+                for (int p = 0; p < nup; ++p) {
+                    h->user_of_dev[base + nm + 2 * p] = ucol + nm + p;
+                    h->user_of_dev[base + nm + 2 * p + 1] = ucol + nm + nup + p;
+                }
+            }
+        }
+    return MF_OK;
+}
+
+EpiParams make_epi(const mf_handle *h) {
+    EpiParams e;
+    memset(&e, 0, sizeof(e));
+    e.n_det = h->n_det;
+    e.n_modes = h->n_modes;
+    e.rank = h->rank;
+    e.M = h->M;
+    for (int mu = 0; mu < h->n_modes; ++mu) {
+        e.ell[mu] = h->ell_m[2 * mu];
+        e.em[mu] = h->ell_m[2 * mu + 1];
+    }
+    for (int k = 0; k < h->n_det; ++k) {
+        e.fp0[k] = (float)h->det[3 * k];
+        e.fx0[k] = (float)h->det[3 * k + 1];
+        double off = (h->det[3 * k + 2] - h->t0) / h->dt;
+        double J = std::floor(off);
+        e.J[k] = (int)J;
+        e.frac[k] = (float)(off - J);
+    }
+    e.inv_dt = (float)(1.0 / h->dt);
+    e.d_ref = (float)h->d_ref;
+    for (int r = 0; r < kStencil; ++r) {
+        e.G4[r] = h->G4[r];
+        e.G5[r] = h->G5[r];
+    }
+    e.basis = h->d_basis;
+    e.bad = h->d_bad;
+    e.n_groups = (int)h->groups.size();
+    e.n_pass = (int)h->passes.size();
+    for (int g = 0; g < e.n_groups; ++g) e.groups[g] = h->groups[g];
+    for (int p = 0; p < e.n_pass; ++p) e.passes[p] = h->passes[p];
+    return e;
+}
+
+RotParams make_rot(const mf_handle *h) {
+    RotParams r;
+    for (int i = 0; i < 16; ++i) r.R[i] = (float)h->R[i];
+    for (int i = 0; i < 4; ++i) r.centre[i] = (float)h->centre[i];
+    r.pre = (float)(h->eps * std::sqrt(1.0 / std::log(2.0)));
+    return r;
+}
+
+int prepare_form(mf_handle *h, mf_form f) {
+    if (!h->have_layout) return MF_E_STATE;
+    free_form(h);
+    h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : 176;
+    int rc = build_layout(h);
+    if (rc) return rc;
+    MF_CUDA(cudaMalloc((void **)&h->d_user_of_dev, sizeof(int) * h->Kdev));
+    MF_CUDA(cudaMemcpy(h->d_user_of_dev, h->user_of_dev.data(), sizeof(int) * h->Kdev,
+                       cudaMemcpyHostToDevice));
+    if (!is_tc_form(f)) {
+        h->Nk = (h->N + h->P + 31) / 32 * 32;
+        MF_CUDA(cudaMalloc((void **)&h->d_W32, sizeof(float) * (size_t)h->Nk * h->Kdev));
+        dim3 grid((h->Kdev + 127) / 128, h->Nk);
+        convert_fp32_kernel<<<grid, 128>>>(h->d_W64, h->N + h->P, h->K, h->d_user_of_dev, h->Kdev,
+                                           h->Nk, h->d_W32);
+        MF_CUDA(cudaGetLastError());
+    } else {
+        rc = convert_tc_weights(h, f);
+        if (rc) return rc;
+    }
+    if (h->d_nodes_s) cudaFree(h->d_nodes_s);
+    h->d_nodes_s = nullptr;
+    MF_CUDA(cudaMalloc((void **)&h->d_nodes_s, sizeof(float4) * (size_t)h->Nk));
+    prescale_nodes<<<(h->Nk + 255) / 256, 256>>>(h->d_nodes64, h->N, h->Nk,
+                                                 h->eps * std::sqrt(1.0 / std::log(2.0)),
+                                                 h->d_nodes_s);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaDeviceSynchronize());
+    h->form = f;
+    return MF_OK;
+}
+
+}  // namespace mf
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+const char *mf_error_string(int s) {
+    switch (s) {
+        case MF_OK: return "MF_OK";
+        case MF_E_INVAL: return "MF_E_INVAL: invalid argument";
+        case MF_E_NOMEM: return "MF_E_NOMEM: allocation failed";
+        case MF_E_CUDA: return "MF_E_CUDA: CUDA runtime or library error";
+        case MF_E_ILLCOND: return "MF_E_ILLCOND: RBF system not positive definite";
+        case MF_E_RANGE: return "MF_E_RANGE: queries outside the sampled time window";
+        case MF_E_TIMEOUT: return "MF_E_TIMEOUT: bounded device wait gave up";
+        case MF_E_NOTIMPL: return "MF_E_NOTIMPL: not implemented";
+        case MF_E_STATE: return "MF_E_STATE: handle not configured for this call";
+        default: return "unknown status";
+    }
+}
+
+const char *mf_version(void) { return "mf 0.1 sm_103a"; }
+
+int mf_svd_compress(const double *z, int N, int M, int rank, double *coef, double *basis,
+                    double *sv, void *stream) {
+    if (!z || !coef || !basis || N < 1 || M < 1 || M > 8192 || rank < 1 || rank > N || rank > M)
+        return MF_E_INVAL;
+    return mf::svd_compress(z, N, M, rank, coef, basis, sv, (cudaStream_t)stream);
+}
+
+int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rbf rbf, double eps,
+             int tail_degree, void *stream, mf_handle **out) {
+    if (!out) return MF_E_INVAL;
+    *out = nullptr;
+    if (!nodes || !node_values || N < 1 || N > 65536 || K < 1 || K > 4096 || !(eps > 0) ||
+        tail_degree < -1 || tail_degree > 1)
+        return MF_E_INVAL;
+    if (rbf != MF_RBF_GAUSSIAN) return MF_E_NOTIMPL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return MF_E_CUDA;
+    }
+    mf_handle *h = new (std::nothrow) mf_handle();
+    if (!h) return MF_E_NOMEM;
+    cudaGetDevice(&h->dev);
+    h->N = N;
+    h->K = K;
+    h->eps = eps;
+    h->tail_degree = tail_degree;
+    h->P = tail_degree < 0 ? 0 : (tail_degree == 0 ? 1 : 5);
+    h->nodes_h.assign(nodes, nodes + (size_t)N * 4);
+    int rc = MF_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMalloc((void **)&h->d_nodes64, sizeof(double) * (size_t)N * 4) != cudaSuccess ||
+        cudaMalloc((void **)&h->d_bad, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        mf_free(h);
+        return MF_E_NOMEM;
+    }
+    cudaMemcpy(h->d_nodes64, nodes, sizeof(double) * (size_t)N * 4, cudaMemcpyHostToDevice);
+    cudaMemset(h->d_bad, 0, sizeof(unsigned long long));
+    rc = mf::rbf_build(h, node_values, st);
+    if (rc == MF_OK) rc = mf::compute_stencil(h);
+    if (rc != MF_OK) {
+        mf_free(h);
+        return rc;
+    }
+    *out = h;
+    return MF_OK;
+}
+
+int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m, int rank) {
+    if (!h || !ell_m || n_det < 1 || n_det > mf::kMaxDet || n_modes < 1 ||
+        n_modes > mf::kMaxModes || rank < 1 || rank > 128)
+        return MF_E_INVAL;
+    if (h->K != n_det * n_modes * 2 * rank + n_det * n_modes * n_modes) return MF_E_INVAL;
+    for (int i = 0; i < n_modes; ++i)
+        if (!supported_mode(ell_m[2 * i], ell_m[2 * i + 1])) return MF_E_NOTIMPL;
+    h->n_det = n_det;
+    h->n_modes = n_modes;
+    h->rank = rank;
+    h->ell_m.assign(ell_m, ell_m + 2 * n_modes);
+    h->have_layout = true;
+    h->have_basis = false;
+    h->have_det = false;
+    return mf::prepare_form(h, h->form);
+}
+
+int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, double dt) {
+    if (!h || !basis || M < mf::kStencil || !(dt > 0)) return MF_E_INVAL;
+    if (!h->have_layout) return MF_E_STATE;
+    size_t n = (size_t)h->n_det * h->n_modes * h->rank * M;
+    std::vector<float2> tmp(n);
+    for (size_t i = 0; i < n; ++i) tmp[i] = make_float2((float)basis[2 * i], (float)basis[2 * i + 1]);
+    if (h->d_basis) cudaFree(h->d_basis);
+    h->d_basis = nullptr;
+    MF_CUDA(cudaMalloc((void **)&h->d_basis, sizeof(float2) * n));
+    MF_CUDA(cudaMemcpy(h->d_basis, tmp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    h->M = M;
+    h->t0 = t0;
+    h->dt = dt;
+    h->have_basis = true;
+    return MF_OK;
+}
+
+int mf_set_detectors(mf_handle *h, const double *det, double d_ref) {
+    if (!h || !det || !(d_ref > 0)) return MF_E_INVAL;
+    if (!h->have_layout) return MF_E_STATE;
+    h->det.assign(det, det + 3 * h->n_det);
+    h->d_ref = d_ref;
+    h->have_det = true;
+    return MF_OK;
+}
+
+int mf_set_rotation(mf_handle *h, const double *metric, const double *centre) {
+    if (!h) return MF_E_INVAL;
+    if (metric) {
+        double R[16];
+        int rc = mf::metric_eig(metric, R);
+        if (rc) return rc;
+        memcpy(h->R, R, sizeof(R));
+    } else {
+        for (int i = 0; i < 16; ++i) h->R[i] = (i % 5 == 0) ? 1.0 : 0.0;
+    }
+    for (int i = 0; i < 4; ++i) h->centre[i] = centre ? centre[i] : 0.0;
+    return MF_OK;
+}
+
+int mf_set_form(mf_handle *h, mf_form f) {
+    if (!h || f < MF_FORM_FP32 || f > MF_FORM_FP16_3TERM) return MF_E_INVAL;
+    if (!h->have_layout) {
+        h->form = f;
+        return MF_OK;
+    }
+    if (f == h->form && (h->d_W32 || h->d_Whi)) return MF_OK;
+    return mf::prepare_form(h, f);
+}
+
+static int ensure_partial(mf_handle *h, size_t need) {
+    if (need <= h->partial_cap) return MF_OK;
+    if (h->d_partial) cudaFree(h->d_partial);
+    h->d_partial = nullptr;
+    h->partial_cap = 0;
+    MF_CUDA(cudaMalloc((void **)&h->d_partial, sizeof(float) * need));
+    h->partial_cap = need;
+    return MF_OK;
+}
+
+int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int Q, int E,
+               float *out_lnL, void *stream) {
+    if (!h || Q < 0 || Q > (1 << 26) || E < 5) return MF_E_INVAL;
+    if (Q == 0) return MF_OK;
+    if (!intrinsic || !extrinsic || !out_lnL) return MF_E_INVAL;
+    if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int np = (int)h->passes.size();
+    float *partial = nullptr;
+    if (np > 1) {
+        int rc = ensure_partial(h, (size_t)np * Q);
+        if (rc) return rc;
+        partial = h->d_partial;
+    }
+    if (h->timing) MF_CUDA(cudaEventRecord(h->ev0, st));
+    int rc = is_tc_form(h->form) ? mf::launch_tc(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial)
+                                 : mf::launch_fp32(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial);
+    if (rc) return rc;
+    if (h->timing) MF_CUDA(cudaEventRecord(h->ev1, st));
+    if (np > 1) return mf::launch_combine(partial, np, Q, out_lnL, st, h->d_bad);
+    return MF_OK;
+}
+
+int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *out, void *stream) {
+    if (!h || Q < 0 || Q > (1 << 26)) return MF_E_INVAL;
+    if (Q == 0) return MF_OK;
+    if (!intrinsic || !out) return MF_E_INVAL;
+    if (!h->have_layout) return MF_E_STATE;
+    if (h->form != MF_FORM_FP32) return MF_E_NOTIMPL;
+    return mf::launch_fp32_columns(h, intrinsic, Q, out, (cudaStream_t)stream);
+}
+
+int mf_set_option(mf_handle *h, const char *key, double value) {
+    if (!h || !key) return MF_E_INVAL;
+    std::string k(key);
+    if (k == "timing") {
+        if (value != 0 && !h->ev0) {
+            MF_CUDA(cudaEventCreate(&h->ev0));
+            MF_CUDA(cudaEventCreate(&h->ev1));
+        }
+        h->timing = value != 0;
+        return MF_OK;
+    }
+    if (k == "pass_max") {
+        int v = (int)value;
+        if (v < 16 || v > 512 || v % 16) return MF_E_INVAL;
+        h->pass_max_user = v;
+        if (h->have_layout && is_tc_form(h->form)) return mf::prepare_form(h, h->form);
+        return MF_OK;
+    }
+    if (k == "tc_ctas_per_sm") {
+        int v = (int)value;
+        if (v < 1 || v > 2) return MF_E_INVAL;
+        h->tc_ctas_per_sm = v;
+        return MF_OK;
+    }
+    return MF_E_INVAL;
+}
+
+int mf_sync_status(mf_handle *h, void *stream, long long *n_bad) {
+    if (!h) return MF_E_INVAL;
+    MF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned long long b = 0;
+    MF_CUDA(cudaMemcpy(&b, h->d_bad, sizeof(b), cudaMemcpyDeviceToHost));
+    MF_CUDA(cudaMemset(h->d_bad, 0, sizeof(b)));
+    if (n_bad) *n_bad = (long long)b;
+    return b ? MF_E_RANGE : MF_OK;
+}
+
+int mf_query(const mf_handle *h, const char *key, double *value) {
+    if (!h || !key || !value) return MF_E_INVAL;
+    std::string k(key);
+    if (k == "cond") *value = h->cond;
+    else if (k == "lambda_min") *value = h->lam_min;
+    else if (k == "lambda_max") *value = h->lam_max;
+    else if (k == "cancel") *value = h->cancel;
+    else if (k == "N") *value = h->N;
+    else if (k == "K") *value = h->K;
+    else if (k == "n_pass") *value = (double)h->passes.size();
+    else if (k == "Kdev") *value = h->Kdev;
+    else if (k == "form") *value = (double)h->form;
+    else if (k == "launches") *value = 1.0 + (h->passes.size() > 1 ? 1.0 : 0.0);
+    else if (k == "kernel_ms") {
+        if (!h->timing) return MF_E_STATE;
+        float ms = 0.f;
+        MF_CUDA(cudaEventSynchronize(h->ev1));
+        MF_CUDA(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+        *value = ms;
+    }
+    else return MF_E_INVAL;
+    return MF_OK;
+}
+
+int mf_get_weights(const mf_handle *h, double *W_host, size_t count) {
+    if (!h || !W_host || count < (size_t)(h->N + h->P) * h->K) return MF_E_INVAL;
+    MF_CUDA(cudaMemcpy(W_host, h->d_W64, sizeof(double) * (size_t)(h->N + h->P) * h->K,
+                       cudaMemcpyDeviceToHost));
+    return MF_OK;
+}
+
+void mf_free(mf_handle *h) {
+    if (!h) return;
+    free_form(h);
+    if (h->d_nodes64) cudaFree(h->d_nodes64);
+    if (h->d_W64) cudaFree(h->d_W64);
+    if (h->d_basis) cudaFree(h->d_basis);
+    if (h->d_nodes_s) cudaFree(h->d_nodes_s);
+    if (h->d_bad) cudaFree(h->d_bad);
+    if (h->d_partial) cudaFree(h->d_partial);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,186 @@
+// Per-query epilogue of the fused lnL kernels: extrinsic amplitudes, spline
+// stencil at each detector delay, SVD-basis reconstruction of the overlaps and
+// the Hermitian cross-term form.  Shared by the FP32 SIMT kernel and the
+// tcgen05 kernels; the caller supplies an accessor that loads 8 consecutive
+// interpolated columns of this query's row.
+#pragma once
+
+#include "mf_internal.cuh"
+
+namespace mf {
+
+// -2Y_lm(iota, phi) = A(iota) e^{i m phi}.  Closed forms in
+// c2 = cos^2(iota/2), s2 = sin^2(iota/2), cs = cos(iota/2) sin(iota/2),
+// obtained from the Wigner-d representation of spin-weighted harmonics
+// (Eq. h_spherical_harmonic_basis); Ap is the +m amplitude, Am the -m one.
+__device__ __forceinline__ void ylm_amps(int l, int m, float c2, float s2, float cs,
+                                         float &Ap, float &Am) {
+    const float k22 = 0.63078313050504f;   // sqrt(5)/(2 sqrt(pi))
+    const float k21 = 1.26156626101008f;   // sqrt(5)/sqrt(pi)
+    const float k33 = 1.82818319785786f;   // sqrt(42)/(2 sqrt(pi))
+    const float k32 = 0.74635266518023f;   // sqrt(7)/(2 sqrt(pi))
+    const float k44 = 4.47811599108140f;   // 3 sqrt(7)/sqrt(pi)
+    switch (l * 10 + m) {
+        case 22: Ap = k22 * c2 * c2; Am = k22 * s2 * s2; break;
+        case 21: Ap = k21 * c2 * cs; Am = k21 * s2 * cs; break;
+        case 33: Ap = -k33 * c2 * c2 * cs; Am = k33 * s2 * s2 * cs; break;
+        case 32: Ap = k32 * c2 * c2 * (c2 - 5.f * s2); Am = k32 * s2 * s2 * (5.f * c2 - s2); break;
+        case 44: Ap = k44 * c2 * c2 * cs * cs; Am = k44 * s2 * s2 * cs * cs; break;
+        default: Ap = 0.f; Am = 0.f; break;
+    }
+}
+
+struct QueryExt {
+    float a;            // d_ref / d_L
+    float c2, s2, cs;   // half-angle combinations of iota
+    float c2p, s2p;     // cos 2psi, sin 2psi
+    float cph, sph;     // cos phi_c, sin phi_c
+    float tc;
+};
+
+__device__ __forceinline__ QueryExt load_ext(const EpiParams &P, const float *ext, int E, int q) {
+    const float *e = ext + (size_t)q * E;
+    QueryExt x;
+    float dL = e[0], ci = e[1], psi = e[2], phc = e[3];
+    x.tc = e[4];
+    x.a = P.d_ref / dL;
+    ci = fminf(1.f, fmaxf(-1.f, ci));
+    x.c2 = 0.5f * (1.f + ci);
+    x.s2 = 0.5f * (1.f - ci);
+    x.cs = 0.5f * sqrtf(fmaxf(0.f, (1.f - ci) * (1.f + ci)));
+    sincosf(2.f * psi, &x.s2p, &x.c2p);
+    sincosf(phc, &x.sph, &x.cph);
+    return x;
+}
+
+// c_k,mu = (d_ref/d_L)/2 e^{-i m phi_c} [F+ (A- + (-1)^l A+) + i Fx (A- - (-1)^l A+)]
+// (Eqs. hplus_hcross_decomposed1/2 in Eq. projected_h_fd).
+template <int NM>
+__device__ __forceinline__ void det_amplitudes(const EpiParams &P, int k, const QueryExt &x,
+                                               float (&cre)[NM], float (&cim)[NM]) {
+    float fp = P.fp0[k] * x.c2p + P.fx0[k] * x.s2p;
+    float fx = -P.fp0[k] * x.s2p + P.fx0[k] * x.c2p;
+#pragma unroll
+    for (int mu = 0; mu < NM; ++mu) {
+        int l = P.ell[mu], m = P.em[mu];
+        float Ap, Am;
+        ylm_amps(l, m, x.c2, x.s2, x.cs, Ap, Am);
+        float sg = (l & 1) ? -1.f : 1.f;
+        float re = 0.5f * x.a * fp * (Am + sg * Ap);
+        float im = 0.5f * x.a * fx * (Am - sg * Ap);
+        // multiply by e^{-i m phi}
+        float er = 1.f, ei = 0.f;
+        for (int t = 0; t < m; ++t) {
+            float nr = er * x.cph + ei * x.sph;
+            float ni = ei * x.cph - er * x.sph;
+            er = nr; ei = ni;
+        }
+        cre[mu] = re * er - im * ei;
+        cim[mu] = re * ei + im * er;
+    }
+}
+
+// Spline stencil for detector k: sample window start and 10 weights of the
+// not-a-knot cubic through samples j-4..j+5 evaluated at u in [0,1).
+// Returns false when the window leaves [0, M).
+__device__ __forceinline__ bool det_stencil(const EpiParams &P, int k, float tc, int &start,
+                                            float (&w)[kStencil]) {
+    float v = fmaf(tc, P.inv_dt, P.frac[k]);
+    if (!(fabsf(v) < 1.0e7f)) {   // NaN / absurd times: no stencil
+        start = -1;
+#pragma unroll
+        for (int r = 0; r < kStencil; ++r) w[r] = 0.f;
+        return false;
+    }
+    float fl = floorf(v);
+    float u = v - fl;
+    int j = P.J[k] + (int)fl;
+    start = j - kStencilLo;
+    float om = 1.f - u;
+    float A = (om * om * om - om) * (1.f / 6.f);
+    float B = (u * u * u - u) * (1.f / 6.f);
+#pragma unroll
+    for (int r = 0; r < kStencil; ++r) w[r] = A * P.G4[r] + B * P.G5[r];
+    w[kStencilLo] += om;
+    w[kStencilLo + 1] += u;
+    return start >= 0 && start + kStencil <= P.M;
+}
+
+// lnL contribution of the groups of one pass for one query.  Acc provides
+//   __device__ void load8(int col, float (&f)[8]);
+// returning columns [col, col+8) of this query's row of the pass.
+template <int NM, class Acc>
+__device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, const QueryExt &x,
+                                          Acc &acc, bool &bad) {
+    float lnl = 0.f;
+    int cur = -1, start = 0;
+    bool ok = true;
+    float w[kStencil];
+    float cre[NM], cim[NM];
+    for (int g = ps.g0; g < ps.g0 + ps.ng; ++g) {
+        const Group G = P.groups[g];
+        if (G.det != cur) {
+            cur = G.det;
+            ok = det_stencil(P, cur, x.tc, start, w);
+            det_amplitudes<NM>(P, cur, x, cre, cim);
+        }
+        if (G.kind == 0) {
+            if (!ok) { bad = true; continue; }
+            const float2 *bp = P.basis + ((size_t)(G.det * P.n_modes + G.mode) * P.rank) * P.M + start;
+            float zr = 0.f, zi = 0.f;
+            for (int i0 = 0; i0 < P.rank; i0 += 4) {
+                float f[8];
+                acc.load8(G.col + 2 * i0, f);
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    int i = i0 + t;
+                    if (i < P.rank) {
+                        const float2 *b = bp + (size_t)i * P.M;
+                        float br = 0.f, bi = 0.f;
+#pragma unroll
+                        for (int r = 0; r < kStencil; ++r) {
+                            float2 v = __ldg(b + r);
+                            br = fmaf(w[r], v.x, br);
+                            bi = fmaf(w[r], v.y, bi);
+                        }
+                        zr += f[2 * t] * br - f[2 * t + 1] * bi;
+                        zi += f[2 * t] * bi + f[2 * t + 1] * br;
+                    }
+                }
+            }
+            float mr = 0.f, mi = 0.f;
+#pragma unroll
+            for (int mu = 0; mu < NM; ++mu)
+                if (mu == G.mode) { mr = cre[mu]; mi = cim[mu]; }
+            lnl += mr * zr + mi * zi;
+        } else {
+            constexpr int NS = NM * NM;
+            constexpr int NL = (NS + 7) / 8;
+            float f[NL * 8];
+#pragma unroll
+            for (int c = 0; c < NL; ++c) {
+                float t8[8];
+                acc.load8(G.col + 8 * c, t8);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) f[8 * c + e] = t8[e];
+            }
+            float quad = 0.f;
+#pragma unroll
+            for (int mu = 0; mu < NM; ++mu) quad += (cre[mu] * cre[mu] + cim[mu] * cim[mu]) * f[mu];
+            int p = NM;
+#pragma unroll
+            for (int mu = 0; mu < NM; ++mu)
+#pragma unroll
+                for (int nu = mu + 1; nu < NM; ++nu) {
+                    float xr = cre[mu] * cre[nu] + cim[mu] * cim[nu];
+                    float xi = cre[mu] * cim[nu] - cim[mu] * cre[nu];
+                    quad += 2.f * (xr * f[p] - xi * f[p + 1]);
+                    p += 2;
+                }
+            lnl -= 0.5f * quad;
+        }
+    }
+    return lnl;
+}
+
+}  // namespace mf

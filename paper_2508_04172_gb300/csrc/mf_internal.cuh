@@ -1,0 +1,153 @@
+// Internal definitions shared by the libmf translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <vector>
+#include <string>
+
+#include "../../include/mf.h"
+
+namespace mf {
+
+constexpr int kMaxDet = 8;
+constexpr int kMaxModes = 5;
+constexpr int kMaxGroups = kMaxDet * (kMaxModes + 1);
+constexpr int kMaxPass = kMaxGroups;
+constexpr int kStencil = 10;          // spline samples j-4 .. j+5
+constexpr int kStencilLo = 4;         // samples before the evaluation interval
+constexpr int kTile = 128;            // queries per tile (one TMEM lane each)
+constexpr int kGroupAlign = 8;        // every column group padded to 8 columns
+constexpr int kPassAlign = 16;        // pass width multiple of 16 (MMA N granularity)
+
+// One column group of the device layout: a detector/mode overlap block
+// (interleaved Re/Im of `rank` SVD coefficients) or a detector's cross-term
+// block (n_modes diagonals then interleaved Re/Im of the strict upper
+// triangle).
+struct Group {
+    int kind;     // 0 = overlap z_k,mu ; 1 = cross terms sigma_k
+    int det;
+    int mode;     // overlap groups only
+    int col;      // first device column of the group, relative to its pass
+    int width;    // padded width (multiple of kGroupAlign)
+};
+
+struct Pass {
+    int col0;     // first device column of the pass (in the device layout)
+    int width;    // padded width (multiple of kPassAlign)
+    int g0, ng;   // groups [g0, g0+ng)
+};
+
+// Everything the per-query epilogue needs; passed by value to kernels.
+struct EpiParams {
+    int n_det, n_modes, rank, M;
+    int ell[kMaxModes], em[kMaxModes];
+    float fp0[kMaxDet], fx0[kMaxDet];
+    int J[kMaxDet];          // integer part of (dt_k - t0)/dt
+    float frac[kMaxDet];     // fractional part of (dt_k - t0)/dt
+    float inv_dt;            // 1/dt
+    float d_ref;
+    float G4[kStencil], G5[kStencil];   // rows 4 and 5 of the spline 2nd-derivative operator
+    const float2 *basis;     // [n_det][n_modes][rank][M]
+    unsigned long long *bad; // out-of-window counter
+    Group groups[kMaxGroups];
+    Pass passes[kMaxPass];
+    int n_groups, n_pass;
+};
+
+struct RotParams {
+    float R[16];
+    float centre[4];
+    float pre;               // eps * sqrt(log2 e): exp(-(eps r)^2) = exp2(-|pre (x - y)|^2)
+};
+
+}  // namespace mf
+
+struct mf_handle {
+    int dev = 0;
+    int N = 0, K = 0, P = 0, tail_degree = 1;
+    double eps = 0.0;
+    mf_rbf rbf = MF_RBF_GAUSSIAN;
+    // FP64 results of the build
+    double *d_nodes64 = nullptr;   // [N][4]
+    double *d_W64 = nullptr;       // [(N+P)][K] (user column order)
+    double cond = 0, lam_min = 0, lam_max = 0, cancel = 0;
+    std::vector<double> nodes_h;   // host copy [N][4]
+    // layout
+    bool have_layout = false, have_basis = false, have_det = false;
+    int n_det = 0, n_modes = 0, rank = 0, M = 0;
+    std::vector<int> ell_m;
+    double t0 = 0, dt = 0, d_ref = 100.0;
+    std::vector<double> det;       // [n_det][3]
+    float2 *d_basis = nullptr;
+    // rotation
+    double R[16] = {1,0,0,0, 0,1,0,0, 0,0,1,0, 0,0,0,1};
+    double centre[4] = {0, 0, 0, 0};
+    // device layout & passes (per form family)
+    std::vector<mf::Group> groups;
+    std::vector<mf::Pass> passes;
+    int Kdev = 0;                   // total device columns (sum of pass widths)
+    std::vector<int> user_of_dev;   // device column -> user column (-1: padding)
+    int *d_user_of_dev = nullptr;
+    int pass_max = 256;
+    // weights per form
+    mf_form form = MF_FORM_FP32;
+    int Nk = 0;                     // N + P padded (node dimension of the weights)
+    float *d_W32 = nullptr;         // [Nk][Kdev]
+    float4 *d_nodes_s = nullptr;    // prescaled nodes [Nk] (x,y,z,w) * pre (padding far away)
+    void *d_Whi = nullptr, *d_Wlo = nullptr;  // 16-bit K-major [Kdev][Nk]
+    float *d_colscale = nullptr;    // per device column scale (FP16 forms)
+    mf_form tc_form_built = MF_FORM_FP32;
+    // spline constants (device-computed, copied to host params)
+    float G4[mf::kStencil], G5[mf::kStencil];
+    bool have_stencil = false;
+    // instrumentation / tuning
+    bool timing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int tc_ctas_per_sm = 1;
+    int pass_max_user = 0;          // 0: form default
+    // scratch
+    unsigned long long *d_bad = nullptr;
+    float *d_partial = nullptr;     // [n_pass][Q] partial lnL
+    size_t partial_cap = 0;
+};
+
+namespace mf {
+int cuda_status(cudaError_t e);
+// Diagnostics to stderr when the environment variable MF_LOG is set.
+void log_msg(const char *fmt, ...);
+int build_layout(mf_handle *h);             // groups/passes/device column map
+int prepare_form(mf_handle *h, mf_form f);  // convert weights for a form
+int compute_stencil(mf_handle *h);          // spline operator rows on the GPU
+EpiParams make_epi(const mf_handle *h);
+RotParams make_rot(const mf_handle *h);
+// kernels launchers
+int launch_fp32(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+                cudaStream_t st, float *partial);
+int launch_fp32_columns(mf_handle *h, const float *intr, int Q, float *out, cudaStream_t st);
+int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+              cudaStream_t st, float *partial);
+int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStream_t st,
+                   unsigned long long *bad);
+}  // namespace mf
+
+#define MF_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e__ = (call);                                                  \
+        if (e__ != cudaSuccess) {                                                  \
+            mf::log_msg("%s:%d %s -> %s", __FILE__, __LINE__, #call,               \
+                        cudaGetErrorString(e__));                                  \
+            return mf::cuda_status(e__);                                           \
+        }                                                                          \
+    } while (0)
+
+#define MF_LIBCALL(call)                                                           \
+    do {                                                                           \
+        int s__ = (int)(call);                                                     \
+        if (s__ != 0) {                                                            \
+            mf::log_msg("%s:%d %s -> status %d", __FILE__, __LINE__, #call, s__);   \
+            return MF_E_CUDA;                                                      \
+        }                                                                          \
+    } while (0)
