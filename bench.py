@@ -245,7 +245,9 @@ def run_ours(args):
         for f in forms:
             if "error" in res[f]:
                 continue
+            torch.cuda.nvtx.range_push(f"timed_{f}")
             tot, kern, nl = time_form(m, f, d_th, d_ex, d_out, args.steps, args.warmup, flush)
+            torch.cuda.nvtx.range_pop()
             res[f].update(ms_per_step=statistics.mean(tot), kernel_ms=statistics.mean(kern),
                           launches=nl, step_ms_all=tot)
     if world > 1:
