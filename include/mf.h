@@ -172,6 +172,27 @@ MF_API int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrins
                float *out_lnL, void *stream);
 
 /*
+ * mf_loglike without any device allocation in the call.  The paper has no
+ * counterpart: this is a service for callers that cannot allocate device
+ * memory while they run -- code inside a CUDA stream capture, callers that
+ * give all device memory to their own fixed pool, real-time sampler loops.
+ * Same arguments and results as mf_loglike with the plain FP32 form (the
+ * handle must be in MF_FORM_FP32, else MF_E_STATE).  When the columns need
+ * several passes, the partial sums live in one fixed array of
+ * MF_NOALLOC_MAX_PARTIAL floats (16 MiB) inside the library, which every GPU
+ * that loads the library keeps until the process exits:
+ *   - n_pass * Q above MF_NOALLOC_MAX_PARTIAL returns MF_E_INVAL (n_pass is
+ *     mf_query "n_pass"); nothing is launched.
+ *   - All calls on a device share the array; calls that overlap on the GPU
+ *     (other streams, other handles) race and must be serialised by the caller.
+ *   - The first call on each device looks up the array's device address;
+ *     make it before any stream capture starts.
+ */
+#define MF_NOALLOC_MAX_PARTIAL 4194304
+MF_API int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const float *extrinsic, int Q,
+                              int E, float *out_lnL, void *stream);
+
+/*
  * Interpolated columns only (the Phi.W stage, Eq. rbfcoeff), in the
  * node_values column order: out [Q][K] device FP32.  Asynchronous.
  */

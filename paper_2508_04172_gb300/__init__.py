@@ -56,6 +56,7 @@ def lib():
         L.mf_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
         L.mf_get_weights.argtypes = [vp, vp, ctypes.c_size_t]
         L.mf_set_option.argtypes = [vp, ctypes.c_char_p, dp]
+        L.mf_loglike_noalloc.argtypes = [vp, vp, vp, ip, ip, vp, vp]
         L.mf_free.argtypes = [vp]
         L.mf_free.restype = None
         _lib = L
