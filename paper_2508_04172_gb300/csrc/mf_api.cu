@@ -149,12 +149,9 @@ EpiParams make_epi(const mf_handle *h) {
     }
     e.inv_dt = (float)(1.0 / h->dt);
     e.d_ref = (float)h->d_ref;
-    for (int r = 0; r < kStencil; ++r) {
-        e.G4[r] = h->G4[r];
-        e.G5[r] = h->G5[r];
-    }
-    e.basis = h->d_basis;
+    e.cubic = h->d_cubic;
     e.bad = h->d_bad;
+    e.err = h->d_err;
     e.n_groups = (int)h->groups.size();
     e.n_pass = (int)h->passes.size();
     for (int g = 0; g < e.n_groups; ++g) e.groups[g] = h->groups[g];
@@ -256,13 +253,15 @@ int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rb
     int rc = MF_OK;
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMalloc((void **)&h->d_nodes64, sizeof(double) * (size_t)N * 4) != cudaSuccess ||
-        cudaMalloc((void **)&h->d_bad, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaMalloc((void **)&h->d_bad, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc((void **)&h->d_err, sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         mf_free(h);
         return MF_E_NOMEM;
     }
     cudaMemcpy(h->d_nodes64, nodes, sizeof(double) * (size_t)N * 4, cudaMemcpyHostToDevice);
     cudaMemset(h->d_bad, 0, sizeof(unsigned long long));
+    cudaMemset(h->d_err, 0, sizeof(unsigned int));
     rc = mf::rbf_build(h, node_values, st);
     if (rc == MF_OK) rc = mf::compute_stencil(h);
     if (rc != MF_OK) {
@@ -293,14 +292,9 @@ int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m, int ra
 int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, double dt) {
     if (!h || !basis || M < mf::kStencil || !(dt > 0)) return MF_E_INVAL;
     if (!h->have_layout) return MF_E_STATE;
-    size_t n = (size_t)h->n_det * h->n_modes * h->rank * M;
-    std::vector<float2> tmp(n);
-    for (size_t i = 0; i < n; ++i) tmp[i] = make_float2((float)basis[2 * i], (float)basis[2 * i + 1]);
-    if (h->d_basis) cudaFree(h->d_basis);
-    h->d_basis = nullptr;
-    MF_CUDA(cudaMalloc((void **)&h->d_basis, sizeof(float2) * n));
-    MF_CUDA(cudaMemcpy(h->d_basis, tmp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
     h->M = M;
+    int rc = mf::build_cubic_table(h, basis);
+    if (rc) return rc;
     h->t0 = t0;
     h->dt = dt;
     h->have_basis = true;
@@ -413,9 +407,13 @@ int mf_sync_status(mf_handle *h, void *stream, long long *n_bad) {
     if (!h) return MF_E_INVAL;
     MF_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
     unsigned long long b = 0;
+    unsigned int err = 0;
     MF_CUDA(cudaMemcpy(&b, h->d_bad, sizeof(b), cudaMemcpyDeviceToHost));
+    MF_CUDA(cudaMemcpy(&err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost));
     MF_CUDA(cudaMemset(h->d_bad, 0, sizeof(b)));
+    MF_CUDA(cudaMemset(h->d_err, 0, sizeof(err)));
     if (n_bad) *n_bad = (long long)b;
+    if (err) return MF_E_TIMEOUT;
     return b ? MF_E_RANGE : MF_OK;
 }
 
@@ -455,9 +453,10 @@ void mf_free(mf_handle *h) {
     free_form(h);
     if (h->d_nodes64) cudaFree(h->d_nodes64);
     if (h->d_W64) cudaFree(h->d_W64);
-    if (h->d_basis) cudaFree(h->d_basis);
+    if (h->d_cubic) cudaFree(h->d_cubic);
     if (h->d_nodes_s) cudaFree(h->d_nodes_s);
     if (h->d_bad) cudaFree(h->d_bad);
+    if (h->d_err) cudaFree(h->d_err);
     if (h->d_partial) cudaFree(h->d_partial);
     if (h->ev0) cudaEventDestroy(h->ev0);
     if (h->ev1) cudaEventDestroy(h->ev1);

@@ -80,30 +80,23 @@ __device__ __forceinline__ void det_amplitudes(const EpiParams &P, int k, const 
     }
 }
 
-// Spline stencil for detector k: sample window start and 10 weights of the
-// not-a-knot cubic through samples j-4..j+5 evaluated at u in [0,1).
-// Returns false when the window leaves [0, M).
-__device__ __forceinline__ bool det_stencil(const EpiParams &P, int k, float tc, int &start,
-                                            float (&w)[kStencil]) {
+// Spline interval for detector k: sample j with t_c + dt_k in [t_j, t_j+1)
+// and the offset u in [0,1).  Returns false when the 10-sample window
+// j-4..j+5 leaves [0, M) (j is then clamped so that reads stay in range).
+__device__ __forceinline__ bool det_interval(const EpiParams &P, int k, float tc, int &j,
+                                             float &u) {
     float v = fmaf(tc, P.inv_dt, P.frac[k]);
-    if (!(fabsf(v) < 1.0e7f)) {   // NaN / absurd times: no stencil
-        start = -1;
-#pragma unroll
-        for (int r = 0; r < kStencil; ++r) w[r] = 0.f;
+    if (!(fabsf(v) < 1.0e7f)) {   // NaN / absurd times
+        j = kStencilLo;
+        u = 0.f;
         return false;
     }
     float fl = floorf(v);
-    float u = v - fl;
-    int j = P.J[k] + (int)fl;
-    start = j - kStencilLo;
-    float om = 1.f - u;
-    float A = (om * om * om - om) * (1.f / 6.f);
-    float B = (u * u * u - u) * (1.f / 6.f);
-#pragma unroll
-    for (int r = 0; r < kStencil; ++r) w[r] = A * P.G4[r] + B * P.G5[r];
-    w[kStencilLo] += om;
-    w[kStencilLo + 1] += u;
-    return start >= 0 && start + kStencil <= P.M;
+    u = v - fl;
+    j = P.J[k] + (int)fl;
+    bool ok = (j - kStencilLo >= 0) && (j - kStencilLo + kStencil <= P.M);
+    if (!ok) j = kStencilLo;
+    return ok;
 }
 
 // lnL contribution of the groups of one pass for one query.  Acc provides
@@ -113,20 +106,23 @@ template <int NM, class Acc>
 __device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, const QueryExt &x,
                                           Acc &acc, bool &bad) {
     float lnl = 0.f;
-    int cur = -1, start = 0;
-    bool ok = true;
-    float w[kStencil];
+    int cur = -1, j = 0;
+    float u = 0.f;
     float cre[NM], cim[NM];
     for (int g = ps.g0; g < ps.g0 + ps.ng; ++g) {
         const Group G = P.groups[g];
         if (G.det != cur) {
             cur = G.det;
-            ok = det_stencil(P, cur, x.tc, start, w);
+            // control flow stays warp-uniform (the tcgen05 accessor loads with
+            // .sync.aligned): an out-of-window query reads an in-range
+            // interval and is flagged instead of skipped
+            if (!det_interval(P, cur, x.tc, j, u)) bad = true;
             det_amplitudes<NM>(P, cur, x, cre, cim);
         }
         if (G.kind == 0) {
-            if (!ok) { bad = true; continue; }
-            const float2 *bp = P.basis + ((size_t)(G.det * P.n_modes + G.mode) * P.rank) * P.M + start;
+            // Eq. (SVD) at t_c + dt_k: z = sum_i C_i S_i(u), S_i the spline of
+            // basis vector i on interval j (cubic in u from the table)
+            const float4 *tp = P.cubic + ((size_t)(G.det * P.n_modes + G.mode) * P.M + j) * P.rank * 2;
             float zr = 0.f, zi = 0.f;
             for (int i0 = 0; i0 < P.rank; i0 += 4) {
                 float f[8];
@@ -135,16 +131,11 @@ __device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, co
                 for (int t = 0; t < 4; ++t) {
                     int i = i0 + t;
                     if (i < P.rank) {
-                        const float2 *b = bp + (size_t)i * P.M;
-                        float br = 0.f, bi = 0.f;
-#pragma unroll
-                        for (int r = 0; r < kStencil; ++r) {
-                            float2 v = __ldg(b + r);
-                            br = fmaf(w[r], v.x, br);
-                            bi = fmaf(w[r], v.y, bi);
-                        }
-                        zr += f[2 * t] * br - f[2 * t + 1] * bi;
-                        zi += f[2 * t] * bi + f[2 * t + 1] * br;
+                        float4 c01 = __ldg(tp + 2 * i), c23 = __ldg(tp + 2 * i + 1);
+                        float br = fmaf(u, fmaf(u, fmaf(u, c23.z, c23.x), c01.z), c01.x);
+                        float bi = fmaf(u, fmaf(u, fmaf(u, c23.w, c23.y), c01.w), c01.y);
+                        zr = fmaf(f[2 * t], br, fmaf(-f[2 * t + 1], bi, zr));
+                        zi = fmaf(f[2 * t], bi, fmaf(f[2 * t + 1], br, zi));
                     }
                 }
             }

@@ -49,9 +49,12 @@ struct EpiParams {
     float frac[kMaxDet];     // fractional part of (dt_k - t0)/dt
     float inv_dt;            // 1/dt
     float d_ref;
-    float G4[kStencil], G5[kStencil];   // rows 4 and 5 of the spline 2nd-derivative operator
-    const float2 *basis;     // [n_det][n_modes][rank][M]
+    // per (detector, mode, sample j, coefficient i): the cubic in u in [0,1)
+    // that the not-a-knot spline through samples j-4..j+5 of basis vector i
+    // takes on [j, j+1]; two float4 = (c0, c1), (c2, c3) complex
+    const float4 *cubic;     // [n_det][n_modes][M][rank][2]
     unsigned long long *bad; // out-of-window counter
+    unsigned int *err;       // device status word: bit 0 = bounded wait gave up
     Group groups[kMaxGroups];
     Pass passes[kMaxPass];
     int n_groups, n_pass;
@@ -81,7 +84,7 @@ struct mf_handle {
     std::vector<int> ell_m;
     double t0 = 0, dt = 0, d_ref = 100.0;
     std::vector<double> det;       // [n_det][3]
-    float2 *d_basis = nullptr;
+    float4 *d_cubic = nullptr;      // spline cubic table (see EpiParams::cubic)
     // rotation
     double R[16] = {1,0,0,0, 0,1,0,0, 0,0,1,0, 0,0,0,1};
     double centre[4] = {0, 0, 0, 0};
@@ -101,15 +104,20 @@ struct mf_handle {
     float *d_colscale = nullptr;    // per device column scale (FP16 forms)
     mf_form tc_form_built = MF_FORM_FP32;
     // spline constants (device-computed, copied to host params)
-    float G4[mf::kStencil], G5[mf::kStencil];
+    double G4[mf::kStencil], G5[mf::kStencil];
     bool have_stencil = false;
     // instrumentation / tuning
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int tc_ctas_per_sm = 1;
     int pass_max_user = 0;          // 0: form default
+    // tcgen05 forms: tensor maps (opaque 128-byte CUtensorMap) of W_hi / W_lo
+    alignas(64) unsigned char tmap_hi[128];
+    alignas(64) unsigned char tmap_lo[128];
+    int nbox = 0;                   // rows (device columns) per W tile = widest pass
     // scratch
     unsigned long long *d_bad = nullptr;
+    unsigned int *d_err = nullptr;
     float *d_partial = nullptr;     // [n_pass][Q] partial lnL
     size_t partial_cap = 0;
 };
@@ -121,6 +129,7 @@ void log_msg(const char *fmt, ...);
 int build_layout(mf_handle *h);             // groups/passes/device column map
 int prepare_form(mf_handle *h, mf_form f);  // convert weights for a form
 int compute_stencil(mf_handle *h);          // spline operator rows on the GPU
+int build_cubic_table(mf_handle *h, const double *basis_host);  // spline cubics per interval
 EpiParams make_epi(const mf_handle *h);
 RotParams make_rot(const mf_handle *h);
 // kernels launchers

@@ -318,7 +318,59 @@ __global__ void pick_basis(const cuDoubleComplex *__restrict__ VT, int M, int ra
     if (t < M) Vsel[(size_t)i * M + t] = VT[(size_t)t * M + i];
 }
 
+// Cubic coefficients of the 10-sample not-a-knot spline on [j, j+1]:
+//   S(u) = y4 + u (y5 - y4 - m4/3 - m5/6) + u^2 m4/2 + u^3 (m5 - m4)/6,
+// m4, m5 = knot second derivatives (rows 4, 5 of the spline operator) of the
+// samples y_r = u_i(j - 4 + r).  Entries whose window leaves [0, M) are zero.
+struct Stencil45 { double g4[kStencil], g5[kStencil]; };
+
+__global__ void cubic_table(const double2 *__restrict__ basis, int nblk, int rank, int M,
+                            Stencil45 g, float4 *__restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    int b = blockIdx.z;
+    if (i >= rank || b >= nblk) return;
+    float4 *o = out + (((size_t)b * M + j) * rank + i) * 2;
+    int s0 = j - kStencilLo;
+    if (s0 < 0 || s0 + kStencil > M) {
+        o[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        o[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        return;
+    }
+    const double2 *y = basis + ((size_t)b * rank + i) * M + s0;
+    double m4r = 0, m4i = 0, m5r = 0, m5i = 0;
+    for (int r = 0; r < kStencil; ++r) {
+        double2 v = y[r];
+        m4r += g.g4[r] * v.x; m4i += g.g4[r] * v.y;
+        m5r += g.g5[r] * v.x; m5i += g.g5[r] * v.y;
+    }
+    double2 y4 = y[kStencilLo], y5 = y[kStencilLo + 1];
+    o[0] = make_float4((float)y4.x, (float)y4.y,
+                       (float)(y5.x - y4.x - m4r / 3.0 - m5r / 6.0),
+                       (float)(y5.y - y4.y - m4i / 3.0 - m5i / 6.0));
+    o[1] = make_float4((float)(0.5 * m4r), (float)(0.5 * m4i), (float)((m5r - m4r) / 6.0),
+                       (float)((m5i - m4i) / 6.0));
+}
+
 }  // namespace
+
+int build_cubic_table(mf_handle *h, const double *basis_host) {
+    const int nblk = h->n_det * h->n_modes, rank = h->rank, M = h->M;
+    DevBuf<double2> b;
+    size_t n = (size_t)nblk * rank * M;
+    MF_CUDA(b.alloc(n));
+    MF_CUDA(cudaMemcpy(b.p, basis_host, sizeof(double2) * n, cudaMemcpyHostToDevice));
+    if (h->d_cubic) cudaFree(h->d_cubic);
+    h->d_cubic = nullptr;
+    MF_CUDA(cudaMalloc((void **)&h->d_cubic, sizeof(float4) * 2 * n));
+    Stencil45 g;
+    for (int r = 0; r < kStencil; ++r) { g.g4[r] = h->G4[r]; g.g5[r] = h->G5[r]; }
+    dim3 grid((rank + 31) / 32, M, nblk);
+    cubic_table<<<grid, 32>>>(b.p, nblk, rank, M, g, h->d_cubic);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaDeviceSynchronize());
+    return MF_OK;
+}
 
 void log_msg(const char *fmt, ...) {
     static const bool on = getenv("MF_LOG") != nullptr;
@@ -347,8 +399,8 @@ int compute_stencil(mf_handle *h) {
     double G[2 * kStencil];
     MF_CUDA(cudaMemcpy(G, g.p, sizeof(G), cudaMemcpyDeviceToHost));
     for (int j = 0; j < kStencil; ++j) {
-        h->G4[j] = (float)G[j];
-        h->G5[j] = (float)G[kStencil + j];
+        h->G4[j] = G[j];
+        h->G5[j] = G[kStencil + j];
     }
     h->have_stencil = true;
     return MF_OK;

@@ -105,3 +105,43 @@ def test_forms_report_passes():
     m = _cases.gpu_model("C1")
     assert m.query("n_pass") >= 3
     assert m.query("K") == 528
+
+
+# --------------------------------------------------------------- tcgen05
+TOL_CHOSEN = 0.01
+# Expected accuracy of the other forms on C1 (probe of the arithmetic): the
+# plain 16-bit and weight-split forms lose to the cancellation in the RBF
+# weights (sum |a_n phi_n| / |F| ~ 1e5); they run, but are not chosen.
+LOOSE = {"bf16_3term": 0.2, "fp16_wsplit": 50.0, "bf16_wsplit": 500.0, "fp16": 50.0,
+         "bf16": 500.0}
+
+
+@pytest.mark.parametrize("cfg,Q", [("C0", 1031), ("C1", 1500)])
+def test_tc_fp16_3term_parity(cfg, Q):
+    th, ex = _cases.queries(cfg, Q, seed=9)
+    ref = _cases.oracle_model(cfg).loglike(th, ex)
+    m = _cases.gpu_model(cfg)
+    m.set_form("fp16_3term")
+    try:
+        got = _run(m, th, ex)
+        assert m.sync_status()[0] == 0
+    finally:
+        m.set_form("fp32")
+    err = np.abs(got - ref)
+    assert np.all(np.isfinite(got))
+    assert err.max() <= TOL_CHOSEN, (err.max(), np.median(err))
+
+
+@pytest.mark.parametrize("form", sorted(LOOSE))
+def test_tc_other_forms_run_with_expected_accuracy(form):
+    th, ex = _cases.queries("C1", 700, seed=10)
+    ref = _cases.oracle_model("C1").loglike(th, ex)
+    m = _cases.gpu_model("C1")
+    m.set_form(form)
+    try:
+        got = _run(m, th, ex)
+        assert m.sync_status()[0] == 0
+    finally:
+        m.set_form("fp32")
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= LOOSE[form]
