@@ -203,7 +203,8 @@ MF_API int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *o
  *                mf_loglike (read back with mf_query "kernel_ms"), 0 = off.
  *   "pass_max" : widest column pass (16..512, multiple of 16) the tcgen05
  *                forms may use; re-lays out the weights.
- *   "tc_ctas_per_sm" : persistent CTAs per SM for the tcgen05 forms (1..2). */
+ *   "tc_nbs"   : depth (2..4) of the weight-tile ring of the tcgen05 kernel;
+ *                0 (default) = deepest that fits in shared memory. */
 MF_API int mf_set_option(mf_handle *h, const char *key, double value);
 
 /* Wait for `stream`, then report device-side status accumulated since the

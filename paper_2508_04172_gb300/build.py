@@ -16,6 +16,8 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                 "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr"]
+# extra nvcc flags, e.g. MF_NVCC_FLAGS=-DMF_TRACE for the per-CTA timeline trace
+FLAGS += os.environ.get("MF_NVCC_FLAGS", "").split()
 
 
 def _deps(src):
@@ -25,6 +27,9 @@ def _deps(src):
 
 def _stale(target, deps):
     if not os.path.exists(target):
+        return True
+    stamp = target + ".flags"
+    if (open(stamp).read() if os.path.exists(stamp) else "") != " ".join(FLAGS):
         return True
     t = os.path.getmtime(target)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
@@ -38,6 +43,7 @@ def _compile(src, verbose):
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+    open(obj + ".flags", "w").write(" ".join(FLAGS))
     if verbose:
         sys.stderr.write(r.stderr)
     return obj
@@ -59,6 +65,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
         os.replace(tmp, SO)
+        open(SO + ".flags", "w").write(" ".join(FLAGS))
     return SO
 
 

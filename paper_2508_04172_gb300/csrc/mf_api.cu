@@ -40,9 +40,9 @@ __global__ void prescale_nodes(const double *__restrict__ y, int N, int Nk, doub
                                float4 *__restrict__ out) {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= Nk) return;
-    if (n < N)
-        out[n] = make_float4((float)(pre * y[4 * n]), (float)(pre * y[4 * n + 1]),
-                             (float)(pre * y[4 * n + 2]), (float)(pre * y[4 * n + 3]));
+    if (n < N)   // stored negated: kernels form x - y as x + (-y)
+        out[n] = make_float4((float)(-pre * y[4 * n]), (float)(-pre * y[4 * n + 1]),
+                             (float)(-pre * y[4 * n + 2]), (float)(-pre * y[4 * n + 3]));
     else
         out[n] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -254,14 +254,14 @@ int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rb
     cudaStream_t st = (cudaStream_t)stream;
     if (cudaMalloc((void **)&h->d_nodes64, sizeof(double) * (size_t)N * 4) != cudaSuccess ||
         cudaMalloc((void **)&h->d_bad, sizeof(unsigned long long)) != cudaSuccess ||
-        cudaMalloc((void **)&h->d_err, sizeof(unsigned int)) != cudaSuccess) {
+        cudaMalloc((void **)&h->d_err, 16 * sizeof(unsigned int)) != cudaSuccess) {
         cudaGetLastError();
         mf_free(h);
         return MF_E_NOMEM;
     }
     cudaMemcpy(h->d_nodes64, nodes, sizeof(double) * (size_t)N * 4, cudaMemcpyHostToDevice);
     cudaMemset(h->d_bad, 0, sizeof(unsigned long long));
-    cudaMemset(h->d_err, 0, sizeof(unsigned int));
+    cudaMemset(h->d_err, 0, 16 * sizeof(unsigned int));
     rc = mf::rbf_build(h, node_values, st);
     if (rc == MF_OK) rc = mf::compute_stencil(h);
     if (rc != MF_OK) {
@@ -394,10 +394,10 @@ int mf_set_option(mf_handle *h, const char *key, double value) {
         if (h->have_layout && is_tc_form(h->form)) return mf::prepare_form(h, h->form);
         return MF_OK;
     }
-    if (k == "tc_ctas_per_sm") {
+    if (k == "tc_nbs") {
         int v = (int)value;
-        if (v < 1 || v > 2) return MF_E_INVAL;
-        h->tc_ctas_per_sm = v;
+        if (v != 0 && (v < 2 || v > 4)) return MF_E_INVAL;
+        h->tc_nbs = v;
         return MF_OK;
     }
     return MF_E_INVAL;
@@ -409,9 +409,16 @@ int mf_sync_status(mf_handle *h, void *stream, long long *n_bad) {
     unsigned long long b = 0;
     unsigned int err = 0;
     MF_CUDA(cudaMemcpy(&b, h->d_bad, sizeof(b), cudaMemcpyDeviceToHost));
-    MF_CUDA(cudaMemcpy(&err, h->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    unsigned int ew[16];
+    MF_CUDA(cudaMemcpy(ew, h->d_err, sizeof(ew), cudaMemcpyDeviceToHost));
+    err = ew[0];
+    if (err) {
+        mf::log_msg("device status 0x%x; first give-up k-block+1 per site:", err);
+        for (int i = 1; i < 9; ++i)
+            if (ew[i]) mf::log_msg("  site %d: %u", i - 1, ew[i]);
+    }
     MF_CUDA(cudaMemset(h->d_bad, 0, sizeof(b)));
-    MF_CUDA(cudaMemset(h->d_err, 0, sizeof(err)));
+    MF_CUDA(cudaMemset(h->d_err, 0, sizeof(ew)));
     if (n_bad) *n_bad = (long long)b;
     if (err) return MF_E_TIMEOUT;
     return b ? MF_E_RANGE : MF_OK;
@@ -429,7 +436,8 @@ int mf_query(const mf_handle *h, const char *key, double *value) {
     else if (k == "n_pass") *value = (double)h->passes.size();
     else if (k == "Kdev") *value = h->Kdev;
     else if (k == "form") *value = (double)h->form;
-    else if (k == "launches") *value = 1.0 + (h->passes.size() > 1 ? 1.0 : 0.0);
+    else if (k == "launches")
+        *value = 1.0 + (h->passes.size() > 1 ? 1.0 : 0.0);
     else if (k == "kernel_ms") {
         if (!h->timing) return MF_E_STATE;
         float ms = 0.f;

@@ -9,6 +9,24 @@
 
 namespace mf {
 
+// Read-only global loads with L1 policies: table entries stream through
+// (no L1 allocation) so that they do not evict the node coordinates, which
+// every k-block of every tile re-reads (kept with evict_last).
+__device__ __forceinline__ float4 ldg_stream(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+__device__ __forceinline__ float4 ldg_keep(const float4 *p) {
+    float4 v;
+    asm volatile("ld.global.nc.L1::evict_last.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
 // -2Y_lm(iota, phi) = A(iota) e^{i m phi}.  Closed forms in
 // c2 = cos^2(iota/2), s2 = sin^2(iota/2), cs = cos(iota/2) sin(iota/2),
 // obtained from the Wigner-d representation of spin-weighted harmonics
@@ -124,20 +142,35 @@ __device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, co
             // basis vector i on interval j (cubic in u from the table)
             const float4 *tp = P.cubic + ((size_t)(G.det * P.n_modes + G.mode) * P.M + j) * P.rank * 2;
             float zr = 0.f, zi = 0.f;
+            // table entries of the next 4 coefficients are loaded one chunk
+            // ahead so their latency overlaps the current chunk's math
+            float4 cur[8], nxt[8];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const bool in = t < P.rank;
+                cur[2 * t] = in ? ldg_stream(tp + 2 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                cur[2 * t + 1] = in ? ldg_stream(tp + 2 * t + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             for (int i0 = 0; i0 < P.rank; i0 += 4) {
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const bool in = i0 + 4 + t < P.rank;
+                    nxt[2 * t] = in ? ldg_stream(tp + 2 * (i0 + 4 + t)) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    nxt[2 * t + 1] = in ? ldg_stream(tp + 2 * (i0 + 4 + t) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
                 float f[8];
                 acc.load8(G.col + 2 * i0, f);
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    int i = i0 + t;
-                    if (i < P.rank) {
-                        float4 c01 = __ldg(tp + 2 * i), c23 = __ldg(tp + 2 * i + 1);
-                        float br = fmaf(u, fmaf(u, fmaf(u, c23.z, c23.x), c01.z), c01.x);
-                        float bi = fmaf(u, fmaf(u, fmaf(u, c23.w, c23.y), c01.w), c01.y);
-                        zr = fmaf(f[2 * t], br, fmaf(-f[2 * t + 1], bi, zr));
-                        zi = fmaf(f[2 * t], bi, fmaf(f[2 * t + 1], br, zi));
-                    }
+                    const float4 c01 = cur[2 * t], c23 = cur[2 * t + 1];
+                    float br = fmaf(u, fmaf(u, fmaf(u, c23.z, c23.x), c01.z), c01.x);
+                    float bi = fmaf(u, fmaf(u, fmaf(u, c23.w, c23.y), c01.w), c01.y);
+                    // columns beyond the rank are zero padding (their f are 0)
+                    zr = fmaf(f[2 * t], br, fmaf(-f[2 * t + 1], bi, zr));
+                    zi = fmaf(f[2 * t], bi, fmaf(f[2 * t + 1], br, zi));
                 }
+#pragma unroll
+                for (int t = 0; t < 8; ++t) cur[t] = nxt[t];
             }
             float mr = 0.f, mi = 0.f;
 #pragma unroll

@@ -98,7 +98,7 @@ fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q
                 float v;
                 if (n < N) {
                     float4 y = __ldg(nodes_s + n);
-                    float d0 = xs.x - y.x, d1 = xs.y - y.y, d2 = xs.z - y.z, d3 = xs.w - y.w;
+                    float d0 = xs.x + y.x, d1 = xs.y + y.y, d2 = xs.z + y.z, d3 = xs.w + y.w;   // y negated
                     float r2 = d0 * d0;
                     r2 = fmaf(d1, d1, r2);
                     r2 = fmaf(d2, d2, r2);

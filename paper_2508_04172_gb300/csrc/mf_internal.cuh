@@ -99,7 +99,7 @@ struct mf_handle {
     mf_form form = MF_FORM_FP32;
     int Nk = 0;                     // N + P padded (node dimension of the weights)
     float *d_W32 = nullptr;         // [Nk][Kdev]
-    float4 *d_nodes_s = nullptr;    // prescaled nodes [Nk] (x,y,z,w) * pre (padding far away)
+    float4 *d_nodes_s = nullptr;    // nodes * (-pre) [Nk] (negated, prescaled; padding zero)
     void *d_Whi = nullptr, *d_Wlo = nullptr;  // 16-bit K-major [Kdev][Nk]
     float *d_colscale = nullptr;    // per device column scale (FP16 forms)
     mf_form tc_form_built = MF_FORM_FP32;
@@ -109,7 +109,7 @@ struct mf_handle {
     // instrumentation / tuning
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    int tc_ctas_per_sm = 1;
+    int tc_nbs = 0;                 // W ring depth of the tcgen05 kernel (0: automatic)
     int pass_max_user = 0;          // 0: form default
     // tcgen05 forms: tensor maps (opaque 128-byte CUtensorMap) of W_hi / W_lo
     alignas(64) unsigned char tmap_hi[128];

@@ -1,23 +1,9 @@
 // tcgen05 forms of the fused lnL kernel (BF16 / FP16 inputs, FP32 accumulation
-// in tensor memory), sm_103a.
-//
-// One CTA evaluates one (128-query tile, column pass) work item, the same
-// decomposition as the FP32 SIMT kernel:
-//   warp 0      : TMA producer -- W tiles (device columns x 32 nodes, K-major,
-//                 64-byte swizzle) for the 1-2 weight parts (hi, lo),
-//   warp 1      : allocates the TMEM accumulator (128 lanes x pass width FP32)
-//                 and one elected thread issues tcgen05.mma (kind::f16):
-//                 Phi_hi.W_hi [+ Phi_hi.W_lo [+ Phi_lo.W_hi]] per 16-node step,
-//   warps 2..5  : one query row per thread (= its TMEM lane): rotate into the
-//                 metric eigenbasis, Gaussian RBF values / tail monomials for
-//                 32 nodes per stage in registers (Eq. rbfcoeff), split to
-//                 16-bit hi (+ lo), store them swizzled as the MMA A operand;
-//                 after the last stage the same threads read their row of the
-//                 accumulator (tcgen05.ld) and run the epilogue (SVD
-//                 reconstruction at each detector delay, amplitudes, cross
-//                 terms: Eqs. SVD, projected_h_fd, logl_complete).
-// Stages are double-buffered with mbarriers; every wait is bounded and sets a
-// status bit instead of hanging.
+// in tensor memory), sm_103a: a persistent, warp-specialised kernel (see
+// tc_kernel) with the RBF matrix tile generated in registers as the MMA A
+// operand, TMA-staged weight tiles as the B operand, and a double-buffered
+// TMEM accumulator so that the per-query epilogue of one work item overlaps
+// the contraction of the next.
 #include "mf_epilogue.cuh"
 
 #include <cuda.h>
@@ -29,12 +15,30 @@
 namespace mf {
 namespace {
 
-constexpr int kKB = 32;                 // nodes per stage (64 bytes of 16-bit values per row)
-constexpr int kStages = 2;
-constexpr int kThreads = 192;           // 6 warps
-constexpr int kRowBytes = kKB * 2;      // 64
-constexpr int kATile = kTile * kRowBytes;   // 8 KB per 16-bit A part
+constexpr int kKB = 32;                 // nodes per k-block (32 -> 64-byte rows, 64 -> 128-byte rows)
+constexpr int kSwz = kKB * 2;           // swizzle span = row bytes (64 or 128)
+constexpr int kMaxStages = 6;           // ring depth bound for the A and W rings
+constexpr int kProdWarps = 8;           // Phi producer warps (2 rows x 8 nodes per thread per k-block)
+constexpr int kEpiWarps = 4;            // epilogue warps (one accumulator row per thread)
+constexpr int kNodeAhead = 4;           // node blocks loaded ahead by each producer warp
+constexpr int kMaxCluster = 8;          // passes per tile = CTAs per cluster (portable limit)
+constexpr int kSlotsPerProducer = 2;    // A slots owned by each CTA of the cluster
+constexpr int kThreads = 32 * (2 + kProdWarps + kEpiWarps);   // 448
+constexpr int kAccCols = 256;           // TMEM columns per accumulator buffer (2 buffers)
+constexpr int kRowBytes = kKB * 2;      // bytes per A/B row
+constexpr int kATile = kTile * kRowBytes;   // bytes per 16-bit A part
+
+#ifdef MF_TRACE
+// Development timeline: per CTA, 16 globaltimer stamps / accumulated waits.
+__device__ unsigned long long g_trace[4096 * 16];
+#define TRACE_SET(i, v) g_trace[(blockIdx.y * gridDim.x + blockIdx.x) * 16 + (i)] = (v)
+#define TRACE_ADD(i, v) atomicAdd(&g_trace[(blockIdx.y * gridDim.x + blockIdx.x) * 16 + (i)], (v))
+#else
+#define TRACE_SET(i, v)
+#define TRACE_ADD(i, v)
+#endif
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
+constexpr uint32_t kSuspendNs = 20000;          // try_wait suspend-time hint
 
 // ------------------------------------------------------------- PTX helpers
 __device__ __forceinline__ uint32_t su32(const void *p) {
@@ -50,13 +54,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes)
                  : "memory");
 }
+// try_wait with a suspend-time hint: a waiting thread sleeps (up to the hint)
+// instead of re-issuing, so waiting warps leave issue slots to working ones.
 __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
+        : "r"(su32(b)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -65,16 +71,19 @@ __device__ __forceinline__ uint64_t gtimer_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Bounded wait: false (and status bit set) if the phase has not completed
-// after kWaitNs nanoseconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, unsigned *err) {
+// Bounded wait: false if the phase has not completed after kWaitNs
+// nanoseconds; then bit 0 of the status word and bit `site` are set, and
+// err[1 + site] records (k-block + 1) of the first give-up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, uint32_t parity, unsigned *err, int site = 0,
+                                          int kb = 0) {
     if (mbar_test(b, parity)) return true;
     const uint64_t t0 = gtimer_ns();
     for (uint32_t i = 1;; ++i) {
         if (mbar_test(b, parity)) return true;
-        if ((i & 255) == 0 && gtimer_ns() - t0 > kWaitNs) break;
+        if ((i & 7) == 0 && gtimer_ns() - t0 > kWaitNs) break;
     }
-    atomicOr(err, 1u);
+    atomicOr(err, 1u | (1u << site));
+    atomicCAS(err + 1 + site, 0u, (unsigned)kb + 1u);
     return false;
 }
 __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
@@ -93,15 +102,16 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
-// Shared-memory matrix descriptor: K-major, 64-byte swizzle, 8-row groups
-// 512 bytes apart (SBO), version 1 (sm_100 family).
+// Shared-memory matrix descriptor: K-major, rows of kSwz bytes with a
+// kSwz-byte swizzle, 8-row groups 8*kSwz bytes apart (SBO), version 1
+// (sm_100 family).  Layout codes: 2 = 128-byte swizzle, 4 = 64-byte swizzle.
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);
     d |= (uint64_t)1 << 16;                 // LBO (unused for swizzled K-major)
-    d |= (uint64_t)(512 >> 4) << 32;        // SBO
+    d |= (uint64_t)((8 * kSwz) >> 4) << 32; // SBO
     d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)4 << 61;                 // SWIZZLE_64B
+    d |= (uint64_t)(kSwz == 128 ? 2 : 4) << 61;
     return d;
 }
 // Instruction descriptor, kind::f16: D = F32, A/B = F16 (0) or BF16 (1),
@@ -121,6 +131,41 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      su32(bar))
                  : "memory");
+}
+__device__ __forceinline__ void mma_commit_mc(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(su32(bar)),
+        "h"(mask)
+        : "memory");
+}
+// Shared-memory address of the same location in another CTA of the cluster.
+__device__ __forceinline__ uint32_t map_cta(uint32_t addr, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+// Bulk copy of `bytes` from this CTA's shared memory into another CTA's
+// (cluster address), completing as transaction bytes on that CTA's mbarrier.
+__device__ __forceinline__ void bulk_copy_to_cta(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "r"(src), "r"(bytes), "r"(mbar)
+        : "memory");
+}
+// Named barrier 1 over the 256 producer threads that also ANDs a predicate.
+__device__ __forceinline__ bool bar_and_256(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.and.pred q, 1, 256, p;\n"
+        " selp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ float ex2(float x) {
     float y;
@@ -156,13 +201,35 @@ struct Half2<1> {   // BF16
 struct TmemAcc {
     uint32_t taddr;         // lane quadrant base | column 0 of the accumulator
     const float *scale;     // per-column scale of this pass (FP16 forms), or nullptr
+    __device__ __forceinline__ void load16(int col, float (&f)[16]) const {
+        uint32_t r[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+            "%11, %12, %13, %14, %15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+              "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr + (uint32_t)col));
+        // the wait carries the loaded registers so their uses stay after it,
+        // while independent global loads may still be hoisted above it
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                       "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                       "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+            float v = __uint_as_float(r[e]);
+            f[e] = scale ? v * __ldg(scale + col + e) : v;
+        }
+    }
     __device__ __forceinline__ void load8(int col, float (&f)[8]) const {
         uint32_t r0, r1, r2, r3, r4, r5, r6, r7;
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
             : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3), "=r"(r4), "=r"(r5), "=r"(r6), "=r"(r7)
             : "r"(taddr + (uint32_t)col));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.wait::ld.sync.aligned;"
+                     : "+r"(r0), "+r"(r1), "+r"(r2), "+r"(r3), "+r"(r4), "+r"(r5), "+r"(r6), "+r"(r7));
         uint32_t r[8] = {r0, r1, r2, r3, r4, r5, r6, r7};
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -179,246 +246,417 @@ struct TcArgs {
     const float *colscale;  // [Kdev] (FP16 forms: s_c * 2^-14), nullptr for BF16
     float *out, *partial;
     float phi_log2_scale;   // log2 of the A-operand scale (14 for FP16, 0 for BF16)
+    int n_tiles;            // query tiles of 128
+    int n_clusters;         // clusters launched (each loops over tiles)
+    int sb;                 // W ring depth
 };
 
-// A-operand byte offset of (row r, 16-byte chunk c) in a 64-byte-swizzled tile.
+// A-operand byte offset of (row r, 16-byte chunk c) in a swizzled tile: the
+// chunk index is XORed with address bits [7, 7 + log2(kSwz/16)).
 __device__ __forceinline__ uint32_t a_off(int r, int c) {
+    if (kSwz == 128) return (uint32_t)((r >> 3) * 1024 + (r & 7) * 128 + ((c ^ (r & 7)) << 4));
     return (uint32_t)((r >> 3) * 512 + (r & 7) * 64 + ((c ^ ((r >> 1) & 3)) << 4));
 }
 
+__device__ __forceinline__ void rotate_row(const RotParams &rot, const float *intr, int q, float (&xu)[4]) {
+    float4 th = *reinterpret_cast<const float4 *>(intr + (size_t)q * 4);
+    float d[4] = {th.x - rot.centre[0], th.y - rot.centre[1], th.z - rot.centre[2], th.w - rot.centre[3]};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+        xu[i] = rot.R[4 * i] * d[0] + rot.R[4 * i + 1] * d[1] + rot.R[4 * i + 2] * d[2] + rot.R[4 * i + 3] * d[3];
+}
+
+// Persistent, warp-specialised kernel, one CTA per SM.  A thread-block cluster
+// of n_pass CTAs (rank = column pass) walks over query tiles (tile = cluster
+// index + i * clusters); every CTA accumulates its pass's columns for the
+// tile, and the RBF tile Phi of node block kb is generated only once, by the
+// CTA of rank kb % n_pass, which copies it into the other CTAs' shared memory
+// with bulk DSMEM copies.
+//   warp 0        TMA: W tiles (pass columns x kKB nodes, K-major, swizzled)
+//                 of the 1-2 weight parts into the W ring,
+//   warp 1        TMEM allocation (2 accumulators x 256 columns); one thread
+//                 issues tcgen05.mma kind::f16 (Phi_hi.W_hi [+ Phi_hi.W_lo
+//                 [+ Phi_lo.W_hi]]) per 16-node step into the tile's buffer,
+//   warps 2..9    Phi producers (this CTA's share of the node blocks): 2-4
+//                 rows x 8 nodes per thread; rotation into the metric
+//                 eigenbasis, Gaussian RBF values / tail monomials (Eq.
+//                 rbfcoeff) in registers, 16-bit hi (+lo) parts stored
+//                 swizzled into an A slot owned by this CTA,
+//   warps 10..13  epilogue: thread = accumulator row = query; SVD
+//                 reconstruction at each detector delay, amplitudes, cross
+//                 terms of this pass (Eqs. SVD, projected_h_fd, logl_complete)
+//                 while the MMAs of the next tile fill the other accumulator.
+// Each CTA owns kSlotsPerProducer A slots for the node blocks it makes, so
+// every barrier is waited on phase by phase by its waiters.  Every mbarrier
+// wait is bounded and sets a status bit instead of hanging.
 template <int NM, int AT, int TERMS>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, 1)
 tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
           TcArgs args, RotParams rot, EpiParams epi) {
     constexpr int NA = (TERMS == 3) ? 2 : 1;
     constexpr int NB = (TERMS >= 2) ? 2 : 1;
+    constexpr int SP = kSlotsPerProducer;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int nbox = args.nbox;
-    const int btile = nbox * kRowBytes;
-    uint8_t *sA = smem;                                       // [kStages][NA][8 KB]
-    uint8_t *sB = sA + kStages * NA * kATile;                 // [kStages][NB][btile]
-    float4 *xs_s = (float4 *)(sB + kStages * NB * btile);   // [128] prescaled query coords
-    float4 *xu_s = xs_s + kTile;                              // [128] Delta-e query coords
-    uint64_t *bars = (uint64_t *)(xu_s + kTile);
-    uint64_t *fullA = bars, *fullB = bars + kStages, *empty = bars + 2 * kStages;
-    uint64_t *accb = bars + 3 * kStages;
-    uint32_t *tslot = (uint32_t *)(bars + 3 * kStages + 1);
+    const int np = epi.n_pass;                  // cluster size
+    const int rank = (int)(blockIdx.x % (unsigned)np);   // == %cluster_ctarank
+    const int cid = (int)(blockIdx.x / (unsigned)np);
+    const Pass ps = epi.passes[rank];
+    const int btile = args.nbox * kRowBytes;
+    const int SB = args.sb;
+    const int nslot = np * SP;
+    uint8_t *sA = smem;                                   // [np][SP][NA][kATile]
+    uint8_t *sB = sA + nslot * NA * kATile;               // [SB][NB][btile]
+    float4 *sN = (float4 *)(sB + SB * NB * btile);        // [kProdWarps][2][kKB] node blocks
+    uint64_t *bars = (uint64_t *)(sN + kProdWarps * 2 * kKB);
+    uint64_t *fullA = bars, *emptyA = bars + kMaxCluster * SP;
+    uint64_t *fullB = bars + 2 * kMaxCluster * SP, *emptyB = fullB + kMaxStages;
+    uint64_t *tfull = emptyB + kMaxStages, *tempty = tfull + 2;
+    uint64_t *done = tempty + 2;
+    uint32_t *tslot = (uint32_t *)(done + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pass = blockIdx.y;
-    const Pass ps = epi.passes[pass];
-    const int q0 = blockIdx.x * kTile;
     const int nkb = args.Nk / kKB;
-    const uint32_t tcols = 256;
+    const uint32_t tcols = 2 * kAccCols;
+    const uint32_t abytes = (uint32_t)(NA * kATile);
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(fullA + s, 128);
-            mbar_init(fullB + s, 1);
-            mbar_init(empty + s, 1);
+        for (int i = 0; i < nslot; ++i) {
+            mbar_init(fullA + i, 1);
+            mbar_init(emptyA + i, (uint32_t)np);
         }
-        mbar_init(accb, 1);
+        for (int i = 0; i < SB; ++i) {
+            mbar_init(fullB + i, 1);
+            mbar_init(emptyB + i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(tfull + i, 1);
+            mbar_init(tempty + i, kEpiWarps);
+        }
+        mbar_init(done, 1);
+        // slots filled by other CTAs' bulk copies expect their bytes; this CTA
+        // arms each for its next use (here the first) -- see the MMA loop
+        for (int q = 0; q < np; ++q)
+            if (q != rank)
+                for (int k = 0; k < SP; ++k) mbar_expect_tx(fullA + q * SP + k, abytes);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         su32(tslot)),
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
                      "r"(tcols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
-    __syncthreads();
+    __syncwarp();
+    cluster_sync();         // all barriers of the cluster exist before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tslot;
+#ifdef MF_TRACE
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        TRACE_SET(0, gtimer_ns());
+        TRACE_SET(10, smid);
+    }
+#endif
 
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------------------------------------------- TMA producer
+            // ------------------------------------------------------------ TMA
             const uint32_t bytes = (uint32_t)(NB * btile);
+            int s = 0;              // W ring slot and its phase parity
+            uint32_t ph = 0;
             int issued = 0;
-            for (int kb = 0; kb < nkb; ++kb) {
-                const int s = kb % kStages;
-                const uint32_t ph = (kb / kStages) & 1;
-                if (!mbar_wait(empty + s, ph ^ 1, epi.err)) break;
-                mbar_expect_tx(fullB + s, bytes);
-                tma_load_2d(sB + (s * NB + 0) * btile, &tm_hi, kb * kKB, ps.col0, fullB + s);
-                if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &tm_lo, kb * kKB, ps.col0, fullB + s);
-                issued = kb + 1;
+            bool ok = true;
+            for (int tile = cid; tile < args.n_tiles && ok; tile += args.n_clusters) {
+                for (int kb = 0; kb < nkb; ++kb) {
+#ifdef MF_TRACE
+                    const long long _t = clock64();
+#endif
+                    if (!mbar_wait(emptyB + s, ph ^ 1, epi.err, 1, kb)) { ok = false; break; }
+                    TRACE_ADD(1, (unsigned long long)(clock64() - _t));
+                    mbar_expect_tx(fullB + s, bytes);
+                    tma_load_2d(sB + (s * NB + 0) * btile, &tm_hi, kb * kKB, ps.col0, fullB + s);
+                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &tm_lo, kb * kKB, ps.col0, fullB + s);
+                    ++issued;
+                    if (++s == SB) { s = 0; ph ^= 1; }
+                }
             }
-            // drain: our copies must have landed before the CTA may exit
-            for (int kb = max(0, issued - kStages); kb < issued; ++kb)
-                mbar_wait(fullB + kb % kStages, (kb / kStages) & 1, epi.err);
+            // drain: our last copies must have landed before the CTA may exit
+            for (int k = 0; k < SB && k < issued; ++k) {
+                if (--s < 0) { s = SB - 1; ph ^= 1; }
+                mbar_wait(fullB + s, ph, epi.err, 2, 0);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // ---------------------------------------------------- MMA issuer
-            const uint32_t id = idesc(AT, ps.width);
+            // ------------------------------------------------------------ MMA
+            int use[kMaxCluster];   // node blocks consumed so far from each producer
+            for (int q = 0; q < kMaxCluster; ++q) use[q] = 0;
+            int sb = 0;
+            uint32_t pb = 0;
+            int i = 0;
             bool ok = true;
-            for (int kb = 0; kb < nkb && ok; ++kb) {
-                const int s = kb % kStages;
-                const uint32_t ph = (kb / kStages) & 1;
-                ok = mbar_wait(fullA + s, ph, epi.err) && mbar_wait(fullB + s, ph, epi.err);
-                if (!ok) break;
+            const uint64_t dA0 = sdesc(su32(sA)), dB0 = sdesc(su32(sB));
+            const uint64_t dAstep = (uint64_t)(abytes >> 4), dBstep = (uint64_t)((NB * btile) >> 4);
+            const uint64_t dAlo = (uint64_t)(kATile >> 4), dBlo = (uint64_t)(btile >> 4);
+            const uint32_t id = idesc(AT, ps.width);
+            for (int tile = cid; tile < args.n_tiles && ok; tile += args.n_clusters, ++i) {
+                const int acc = i & 1;
+                const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
+#ifdef MF_TRACE
+                const long long _te = clock64();
+#endif
+                if (!mbar_wait(tempty + acc, (((uint32_t)i >> 1) & 1) ^ 1, epi.err, 8, i)) break;
+                TRACE_ADD(11, (unsigned long long)(clock64() - _te));
                 tc_fence_after();
-                const uint32_t a0 = su32(sA + (s * NA) * kATile);
-                const uint32_t b0 = su32(sB + (s * NB) * btile);
+                int p = 0;          // producer of node block kb = kb % np
+                for (int kb = 0; kb < nkb; ++kb) {
+                    const int u = use[p];
+                    const int sa = p * SP + (u & (SP - 1));
+                    const uint32_t pa = (uint32_t)((u / SP) & 1);
+#ifdef MF_TRACE
+                    long long _t = clock64();
+#endif
+                    if (!mbar_wait(fullA + sa, pa, epi.err, 3, kb)) { ok = false; break; }
+                    TRACE_ADD(2, (unsigned long long)(clock64() - _t));
+#ifdef MF_TRACE
+                    _t = clock64();
+#endif
+                    if (!mbar_wait(fullB + sb, pb, epi.err, 4, kb)) { ok = false; break; }
+                    TRACE_ADD(3, (unsigned long long)(clock64() - _t));
+                    tc_fence_after();
+                    const uint64_t a = dA0 + (uint64_t)sa * dAstep, b = dB0 + (uint64_t)sb * dBstep;
 #pragma unroll
-                for (int k16 = 0; k16 < kKB / 16; ++k16) {
-                    const uint32_t koff = k16 * 32;
-                    const uint32_t acc0 = (kb > 0 || k16 > 0) ? 1u : 0u;
-                    mma_f16(tmem, sdesc(a0 + koff), sdesc(b0 + koff), id, acc0);
-                    if (TERMS >= 2) mma_f16(tmem, sdesc(a0 + koff), sdesc(b0 + btile + koff), id, 1u);
-                    if (TERMS == 3) mma_f16(tmem, sdesc(a0 + kATile + koff), sdesc(b0 + koff), id, 1u);
+                    for (int k16 = 0; k16 < kKB / 16; ++k16) {
+                        const uint64_t ko = (uint64_t)(k16 * 2);      // +32 bytes
+                        mma_f16(d, a + ko, b + ko, id, (kb > 0 || k16 > 0) ? 1u : 0u);
+                        if (TERMS >= 2) mma_f16(d, a + ko, b + dBlo + ko, id, 1u);
+                        if (TERMS == 3) mma_f16(d, a + dAlo + ko, b + ko, id, 1u);
+                    }
+                    mma_commit(emptyB + sb);
+                    mma_commit_mc(emptyA + sa, (uint16_t)(1u << p));   // slot read: tell its producer
+                    if (p != rank) mbar_expect_tx(fullA + sa, abytes);   // arm the slot's next fill
+                    use[p] = u + 1;
+                    if (++sb == SB) { sb = 0; pb ^= 1; }
+                    if (++p == np) p = 0;
                 }
-                mma_commit(empty + s);
+                mma_commit(tfull + acc);
             }
-            mma_commit(accb);
-            // the accumulator must be complete before warp 1 frees TMEM
-            mbar_wait(accb, 0, epi.err);
+            TRACE_SET(4, gtimer_ns());
+            // every MMA this thread issued must be complete before TMEM is freed
+            mma_commit(done);
+            mbar_wait(done, 0, epi.err, 5, 0);
         }
-    } else {
-        // ------------------------------------------ Phi producers / epilogue
-        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
-        const int r = quad * 32 + lane;             // epilogue: query row == TMEM lane
-        const int q = q0 + r;
-        const int qc = min(q, args.Q - 1);
-        {
-            // rotate this row's query into the metric eigenbasis (Sec. II E)
-            float4 th = *reinterpret_cast<const float4 *>(args.intr + (size_t)qc * 4);
-            float d[4] = {th.x - rot.centre[0], th.y - rot.centre[1], th.z - rot.centre[2],
-                          th.w - rot.centre[3]};
-            float xu[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                xu[i] = rot.R[4 * i] * d[0] + rot.R[4 * i + 1] * d[1] + rot.R[4 * i + 2] * d[2] +
-                        rot.R[4 * i + 3] * d[3];
-            xu_s[r] = make_float4(xu[0], xu[1], xu[2], xu[3]);
-            xs_s[r] = make_float4(xu[0] * rot.pre, xu[1] * rot.pre, xu[2] * rot.pre, xu[3] * rot.pre);
-        }
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // producer warps only
-        // producer mapping: 8 consecutive nodes (one 16-byte chunk) for 4 rows
-        const int pidx = threadIdx.x - 64;
-        const int c = pidx & 3, rg = pidx >> 2;
-        float2 X[2][4];     // rows (rg, rg+32) and (rg+64, rg+96), per coordinate
-#pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            float4 a = xs_s[rg + 64 * h2], b = xs_s[rg + 64 * h2 + 32];
-            X[h2][0] = make_float2(a.x, b.x);
-            X[h2][1] = make_float2(a.y, b.y);
-            X[h2][2] = make_float2(a.z, b.z);
-            X[h2][3] = make_float2(a.w, b.w);
-        }
+    } else if (warp < 2 + kProdWarps) {
+        // --------------------------------------------------- Phi producers
+        constexpr int CPR = kKB / 8;                // 16-byte chunks per row
+        constexpr int RS = 256 / CPR;               // row stride between a thread's rows
+        constexpr int RPT = kTile / RS;             // rows per thread (2 or 4)
+        const int pt = threadIdx.x - 64;            // 0..255
+        const int c = pt % CPR, rg = pt / CPR;      // chunk (8 nodes); rows rg + RS j
         const float sc = args.phi_log2_scale;
+        const float2 nsc = make_float2(-sc, -sc);
         const float tsc = exp2f(sc);
+        uint32_t aoff[RPT];
+#pragma unroll
+        for (int j = 0; j < RPT; ++j) aoff[j] = a_off(rg + RS * j, c);
+        int u = 0;              // node blocks produced by this CTA so far
+        int sbuf = 0;           // node scratch buffer (double-buffered)
         bool ok = true;
-        for (int kb = 0; kb < nkb; ++kb) {
-            const int s = kb % kStages;
-            const uint32_t ph = (kb / kStages) & 1;
-            if (!mbar_wait(empty + s, ph ^ 1, epi.err)) { ok = false; break; }
-            uint8_t *ahi = sA + (s * NA) * kATile;
-            const int n0 = kb * kKB + c * 8;
-            float v[4][8];   // [row j][node e], rows rg + 32 j
-            if (kb * kKB + kKB <= args.N) {
+        // this lane's node of the next kNodeAhead node blocks of this CTA (FIFO)
+        float4 yq[kNodeAhead];
+        {
+            int kn = rank;
+#pragma unroll
+            for (int dd = 0; dd < kNodeAhead; ++dd) {
+                yq[dd] = ldg_keep(args.nodes_s + (kn < nkb ? kn : 0) * kKB + lane);
+                kn += np;
+                if (kn >= nkb) kn = rank;
+            }
+        }
+        int kfetch = rank;      // node block whose coordinates enter the FIFO next
+        for (int dd = 0; dd < kNodeAhead; ++dd) { kfetch += np; if (kfetch >= nkb) kfetch = rank; }
+        for (int tile = cid; tile < args.n_tiles && ok; tile += args.n_clusters) {
+            float2 X[RPT / 2][4];   // row pairs (rg + 2h RS, rg + (2h+1) RS), per coordinate
+            float4 xu[RPT];
+            {
+                float a[RPT][4];
+#pragma unroll
+                for (int j = 0; j < RPT; ++j) {
+                    rotate_row(rot, args.intr, min(tile * kTile + rg + RS * j, args.Q - 1), a[j]);
+                    xu[j] = make_float4(a[j][0], a[j][1], a[j][2], a[j][3]);
+                }
+#pragma unroll
+                for (int h2 = 0; h2 < RPT / 2; ++h2)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        X[h2][k] = make_float2(a[2 * h2][k] * rot.pre, a[2 * h2 + 1][k] * rot.pre);
+            }
+            for (int kb = rank; kb < nkb; kb += np) {
+#ifdef MF_TRACE
+                const long long _tp = clock64();
+#endif
+                // node coordinates of this block (pre-negated, pre-scaled): one
+                // coalesced 512-byte load per warp issued kNodeAhead blocks ahead,
+                // shared through the warp's scratch
+                const float4 ycur = yq[0];
+#pragma unroll
+                for (int dd = 0; dd < kNodeAhead - 1; ++dd) yq[dd] = yq[dd + 1];
+                yq[kNodeAhead - 1] = ldg_keep(args.nodes_s + kfetch * kKB + lane);
+                kfetch += np;
+                if (kfetch >= nkb) kfetch = rank;
+                float4 *scr = sN + ((warp - 2) * 2 + sbuf) * kKB;
+                sbuf ^= 1;
+                scr[lane] = ycur;
+                __syncwarp();
+                const int n0 = kb * kKB + c * 8;
+                float v[RPT][8];   // rows rg + RS j, nodes n0 .. n0+7
+                const bool full = (kb * kKB + kKB <= args.N);
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    const float4 y = __ldg(args.nodes_s + n0 + e);
-                    const float2 ny0 = make_float2(-y.x, -y.x), ny1 = make_float2(-y.y, -y.y);
-                    const float2 ny2 = make_float2(-y.z, -y.z), ny3 = make_float2(-y.w, -y.w);
+                    const int n = n0 + e;
+                    if (full || n < args.N) {
+                        const float4 y = scr[c * 8 + e];
+                        const float2 ny0 = make_float2(y.x, y.x), ny1 = make_float2(y.y, y.y);
+                        const float2 ny2 = make_float2(y.z, y.z), ny3 = make_float2(y.w, y.w);
 #pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        float2 d = __fadd2_rn(X[h2][0], ny0);
-                        float2 r2 = __fmul2_rn(d, d);
-                        d = __fadd2_rn(X[h2][1], ny1);
-                        r2 = __ffma2_rn(d, d, r2);
-                        d = __fadd2_rn(X[h2][2], ny2);
-                        r2 = __ffma2_rn(d, d, r2);
-                        d = __fadd2_rn(X[h2][3], ny3);
-                        r2 = __ffma2_rn(d, d, r2);
-                        v[2 * h2][e] = ex2(sc - r2.x);
-                        v[2 * h2 + 1][e] = ex2(sc - r2.y);
-                    }
-                }
-            } else {
-                // last block: RBF values, tail monomials 1, x1..x4, zero padding
-#pragma unroll
-                for (int jj = 0; jj < 4; ++jj) {
-                    const int row = rg + 32 * jj;
-                    const float4 xs = xs_s[row], xu = xu_s[row];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const int n = n0 + e;
-                        float val;
-                        if (n < args.N) {
-                            float4 y = __ldg(args.nodes_s + n);
-                            float d0 = xs.x - y.x, d1 = xs.y - y.y, d2 = xs.z - y.z, d3 = xs.w - y.w;
-                            float r2 = d0 * d0;
-                            r2 = fmaf(d1, d1, r2);
-                            r2 = fmaf(d2, d2, r2);
-                            r2 = fmaf(d3, d3, r2);
-                            val = ex2(sc - r2);
-                        } else {
-                            const int p = n - args.N;
-                            val = (p == 0) ? 1.f : (p == 1) ? xu.x : (p == 2) ? xu.y : (p == 3) ? xu.z : xu.w;
-                            val = (p < args.P) ? val * tsc : 0.f;
+                        for (int h2 = 0; h2 < RPT / 2; ++h2) {
+                            // r2 = |x - y|^2 - sc, so Phi * 2^sc = 2^-r2 (two rows at once)
+                            float2 dd = __fadd2_rn(X[h2][0], ny0);
+                            float2 r2 = __ffma2_rn(dd, dd, nsc);
+                            dd = __fadd2_rn(X[h2][1], ny1);
+                            r2 = __ffma2_rn(dd, dd, r2);
+                            dd = __fadd2_rn(X[h2][2], ny2);
+                            r2 = __ffma2_rn(dd, dd, r2);
+                            dd = __fadd2_rn(X[h2][3], ny3);
+                            r2 = __ffma2_rn(dd, dd, r2);
+                            v[2 * h2][e] = ex2(-r2.x);
+                            v[2 * h2 + 1][e] = ex2(-r2.y);
                         }
-                        v[jj][e] = val;
+                    } else {
+                        // tail monomials 1, x1..x4 (times 2^sc), then zero padding
+                        const int q = n - args.N;
+#pragma unroll
+                        for (int j = 0; j < RPT; ++j) {
+                            float m = (q == 0) ? 1.f : (q == 1) ? xu[j].x : (q == 2) ? xu[j].y : (q == 3) ? xu[j].z : xu[j].w;
+                            v[j][e] = (q < args.P) ? m * tsc : 0.f;
+                        }
                     }
                 }
-            }
-            // 16-bit hi (+ lo) parts, 64-byte swizzled A tile (row = rg + 32 jj)
+                // 16-bit hi (+ lo) parts, computed before waiting for the slot
+                uint4 hi[RPT], lo[RPT];
 #pragma unroll
-            for (int jj = 0; jj < 4; ++jj) {
-                const int row = rg + 32 * jj;
-                uint4 hi;
-                hi.x = Half2<AT>::pack(v[jj][0], v[jj][1]);
-                hi.y = Half2<AT>::pack(v[jj][2], v[jj][3]);
-                hi.z = Half2<AT>::pack(v[jj][4], v[jj][5]);
-                hi.w = Half2<AT>::pack(v[jj][6], v[jj][7]);
-                *reinterpret_cast<uint4 *>(ahi + a_off(row, c)) = hi;
-                if (TERMS == 3) {
-                    float2 h0 = Half2<AT>::unpack(hi.x), h1 = Half2<AT>::unpack(hi.y);
-                    float2 h2 = Half2<AT>::unpack(hi.z), h3 = Half2<AT>::unpack(hi.w);
-                    uint4 lo;
-                    lo.x = Half2<AT>::pack(v[jj][0] - h0.x, v[jj][1] - h0.y);
-                    lo.y = Half2<AT>::pack(v[jj][2] - h1.x, v[jj][3] - h1.y);
-                    lo.z = Half2<AT>::pack(v[jj][4] - h2.x, v[jj][5] - h2.y);
-                    lo.w = Half2<AT>::pack(v[jj][6] - h3.x, v[jj][7] - h3.y);
-                    *reinterpret_cast<uint4 *>(ahi + kATile + a_off(row, c)) = lo;
+                for (int j = 0; j < RPT; ++j) {
+                    hi[j].x = Half2<AT>::pack(v[j][0], v[j][1]);
+                    hi[j].y = Half2<AT>::pack(v[j][2], v[j][3]);
+                    hi[j].z = Half2<AT>::pack(v[j][4], v[j][5]);
+                    hi[j].w = Half2<AT>::pack(v[j][6], v[j][7]);
+                    if (TERMS == 3) {
+                        float2 a = Half2<AT>::unpack(hi[j].x), b = Half2<AT>::unpack(hi[j].y);
+                        float2 cc = Half2<AT>::unpack(hi[j].z), dd = Half2<AT>::unpack(hi[j].w);
+                        lo[j].x = Half2<AT>::pack(v[j][0] - a.x, v[j][1] - a.y);
+                        lo[j].y = Half2<AT>::pack(v[j][2] - b.x, v[j][3] - b.y);
+                        lo[j].z = Half2<AT>::pack(v[j][4] - cc.x, v[j][5] - cc.y);
+                        lo[j].w = Half2<AT>::pack(v[j][6] - dd.x, v[j][7] - dd.y);
+                    }
+                }
+                const int sa = rank * SP + (u & (SP - 1));
+                const uint32_t pa = (uint32_t)((u / SP) & 1);
+#ifdef MF_TRACE
+                const long long _t = clock64();
+                if (pt == 0) TRACE_ADD(14, (unsigned long long)(_t - _tp));
+#endif
+                const bool got = mbar_wait(emptyA + sa, pa ^ 1, epi.err, 6, kb);
+                if (pt == 0) TRACE_ADD(5, (unsigned long long)(clock64() - _t));
+                uint8_t *base = sA + sa * abytes;
+                if (got) {
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j) {
+                        *reinterpret_cast<uint4 *>(base + aoff[j]) = hi[j];
+                        if (TERMS == 3) *reinterpret_cast<uint4 *>(base + kATile + aoff[j]) = lo[j];
+                    }
+                    fence_async_smem();
+                }
+                // all producer warps wrote the slot; and all agree whether to go on
+#ifdef MF_TRACE
+                const long long _tb = clock64();
+#endif
+                if (!bar_and_256(got)) { ok = false; break; }
+                if (pt == 0) TRACE_ADD(15, (unsigned long long)(clock64() - _tb));
+#ifdef MF_TRACE
+                const long long _tc2 = clock64();
+#endif
+                if (pt == 0) {
+                    // local slot: plain arrive; other CTAs: bulk copy completing
+                    // as transaction bytes on their (pre-armed) fullA barrier
+                    const uint32_t src = su32(base), fa = su32(fullA + sa);
+                    for (int dst = 0; dst < np; ++dst)
+                        if (dst != rank) bulk_copy_to_cta(map_cta(src, dst), src, abytes, map_cta(fa, dst));
+                    mbar_arrive(fullA + sa);
+                    TRACE_ADD(12, 0ull);
+                }
+                if (pt == 0) TRACE_ADD(3, 0ull);
+#ifdef MF_TRACE
+                if (pt == 0) TRACE_ADD(13, 0ull);
+                if (pt == 0) atomicAdd(&g_trace[(blockIdx.y * gridDim.x + blockIdx.x) * 16 + 11], (unsigned long long)(clock64() - _tc2));
+#endif
+                ++u;
+            }
+        }
+        if (pt == 0) TRACE_SET(6, gtimer_ns());
+    } else {
+        // ------------------------------------------------------- epilogue
+        const int quad = warp & 3;                  // TMEM lane quadrant of this warp
+        const int r = quad * 32 + lane;             // accumulator row == query in tile
+        int i = 0;
+        for (int tile = cid; tile < args.n_tiles; tile += args.n_clusters, ++i) {
+            const int acc = i & 1;
+            const int q = tile * kTile + r;
+            const int qc = min(q, args.Q - 1);
+            QueryExt x = load_ext(epi, args.ext, args.E, qc);
+#ifdef MF_TRACE
+            const long long _tw = clock64();
+#endif
+            bool ok = mbar_wait(tfull + acc, ((uint32_t)i >> 1) & 1, epi.err, 7, i);
+            if (r == 0) TRACE_ADD(12, (unsigned long long)(clock64() - _tw));
+#ifdef MF_TRACE
+            const long long _tc = clock64();
+#endif
+            ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld below is warp-collective
+            tc_fence_after();
+            float l = __int_as_float(0x7fc00000);
+            if (ok) {
+                TmemAcc tacc{tmem + (uint32_t)(acc * kAccCols) + ((uint32_t)(quad * 32) << 16),
+                             args.colscale ? args.colscale + ps.col0 : nullptr};
+                bool bad = false;
+                l = pass_lnl<NM>(epi, ps, x, tacc, bad);
+                if (bad) l = __int_as_float(0x7fc00000);
+            }
+            if (r == 0) TRACE_ADD(13, (unsigned long long)(clock64() - _tc));
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(tempty + acc);
+            if (q < args.Q) {
+                if (np == 1) {
+                    args.out[q] = l;
+                    if (l != l) atomicAdd(epi.bad, 1ull);
+                } else {
+                    args.partial[(size_t)rank * args.Q + q] = l;
                 }
             }
-            fence_async_smem();
-            mbar_arrive(fullA + s);
+            if (!ok) break;
         }
-        // -------------------------------------------------------- epilogue
-        if (ok) ok = mbar_wait(accb, 0, epi.err);
-        ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld below is warp-collective
-        tc_fence_after();
-        float l = __int_as_float(0x7fc00000);
-        if (ok) {
-            QueryExt x = load_ext(epi, args.ext, args.E, qc);
-            TmemAcc acc{tmem + ((uint32_t)(quad * 32) << 16),
-                        args.colscale ? args.colscale + ps.col0 : nullptr};
-            bool bad = false;
-            l = pass_lnl<NM>(epi, ps, x, acc, bad);
-            if (bad) l = __int_as_float(0x7fc00000);
-        }
-        if (q < args.Q) {
-            if (epi.n_pass == 1) {
-                args.out[q] = l;
-                if (l != l) atomicAdd(epi.bad, 1ull);
-            } else {
-                args.partial[(size_t)pass * args.Q + q] = l;
-            }
-        }
-        tc_fence_before();
+        if (r == 0) TRACE_SET(8, gtimer_ns());
     }
-    __syncthreads();
+    __syncwarp();
+    // no CTA may leave while a peer can still copy into it or signal it
+    cluster_sync();
+    if (threadIdx.x == 0) TRACE_SET(9, gtimer_ns());
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols)
-                     : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
     }
 }
 
@@ -491,7 +729,8 @@ int make_tmap(void *out, void *base, int at, int Nk, int Kdev, int nbox) {
     CUresult r = fn((CUtensorMap *)out,
                     at == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
                     base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    kSwz == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         log_msg("cuTensorMapEncodeTiled failed: %d", (int)r);
@@ -515,17 +754,45 @@ template <int NM, int AT, int TERMS>
 int launch_nm(mf_handle *h, const TcArgs &a, cudaStream_t st) {
     constexpr int NA = (TERMS == 3) ? 2 : 1;
     constexpr int NB = (TERMS >= 2) ? 2 : 1;
-    size_t bytes = 1024 + (size_t)kStages * NA * kATile + (size_t)kStages * NB * h->nbox * kRowBytes +
-                   2 * kTile * sizeof(float4) + (3 * kStages + 2) * 8;
-    bytes = std::max(bytes, (size_t)80 * 1024);   // at most 2 CTAs (2 x 256 TMEM columns) per SM
+    const int np = (int)h->passes.size();
+    if (np > kMaxCluster) return MF_E_NOTIMPL;
+    TcArgs a2 = a;
+    a2.n_tiles = (a.Q + kTile - 1) / kTile;
+    auto smem_for = [&](int sb) {
+        return (size_t)1024 + (size_t)np * kSlotsPerProducer * NA * kATile +
+               (size_t)sb * NB * h->nbox * kRowBytes + (size_t)kProdWarps * 2 * kKB * sizeof(float4) +
+               (2 * kMaxCluster * kSlotsPerProducer + 2 * kMaxStages + 5) * 8 + 16;
+    };
+    a2.sb = h->tc_nbs ? h->tc_nbs : 4;
+    while (smem_for(a2.sb) > 227 * 1024 && a2.sb > 2) --a2.sb;
+    if (smem_for(a2.sb) > 227 * 1024) return MF_E_NOTIMPL;
+    // one CTA per SM (it owns all 512 TMEM columns): request > half the SM's shared memory
+    size_t bytes = std::max(smem_for(a2.sb), (size_t)120 * 1024);
     auto kern = tc_kernel<NM, AT, TERMS>;
     MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    dim3 grid((a.Q + kTile - 1) / kTile, (unsigned)h->passes.size());
+    if (np > 1) MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = bytes;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)np;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // as many clusters as can be resident at once (each then loops over tiles)
+    int max_clusters = 0;
+    cfg.gridDim = dim3((unsigned)np, 1, 1);
+    MF_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
+    if (max_clusters < 1) return MF_E_NOTIMPL;
+    a2.n_clusters = std::min(a2.n_tiles, max_clusters);
+    cfg.gridDim = dim3((unsigned)(a2.n_clusters * np), 1, 1);
     CUtensorMap thi, tlo;
     memcpy(&thi, h->tmap_hi, sizeof(thi));
     memcpy(&tlo, h->tmap_lo, sizeof(tlo));
-    kern<<<grid, kThreads, bytes, st>>>(thi, tlo, a, make_rot(h), make_epi(h));
-    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaLaunchKernelEx(&cfg, kern, thi, tlo, a2, make_rot(h), make_epi(h)));
     return MF_OK;
 }
 
@@ -607,3 +874,13 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
 }
 
 }  // namespace mf
+
+#ifdef MF_TRACE
+extern "C" __attribute__((visibility("default"))) int mf_debug_trace(unsigned long long *host, size_t n) {
+    if (n > 4096 * 16) n = 4096 * 16;
+    if (cudaMemcpyFromSymbol(host, mf::g_trace, n * 8) != cudaSuccess) return MF_E_CUDA;
+    static unsigned long long zero[4096 * 16];
+    if (cudaMemcpyToSymbol(mf::g_trace, zero, sizeof(zero)) != cudaSuccess) return MF_E_CUDA;
+    return MF_OK;
+}
+#endif
