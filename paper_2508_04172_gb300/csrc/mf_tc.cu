@@ -22,7 +22,8 @@ constexpr int kProdWarps = 8;           // Phi producer warps (2 rows x 8 nodes 
 constexpr int kEpiWarps = 4;            // epilogue warps (one accumulator row per thread)
 constexpr int kNodeAhead = 4;           // node blocks loaded ahead by each producer warp
 constexpr int kMaxCluster = 8;          // passes per tile = CTAs per cluster (portable limit)
-constexpr int kSlotsPerProducer = 2;    // A slots owned by each CTA of the cluster
+constexpr int kSlotsPerProducer = 2;    // A slots owned by each CTA of the cluster (the MMA
+                                        // thread's packed per-producer state assumes 2)
 constexpr int kThreads = 32 * (2 + kProdWarps + kEpiWarps);   // 448
 constexpr int kAccCols = 256;           // TMEM columns per accumulator buffer (2 buffers)
 constexpr int kRowBytes = kKB * 2;      // bytes per A/B row
@@ -59,7 +60,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes) {
 __device__ __forceinline__ bool mbar_test(uint64_t *b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
         " selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
         : "r"(su32(b)), "r"(parity), "r"(kSuspendNs)
@@ -392,8 +393,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------------------ MMA
-            int use[kMaxCluster];   // node blocks consumed so far from each producer
-            for (int q = 0; q < kMaxCluster; ++q) use[q] = 0;
+            // per producer p, bits [2p, 2p+2) = (node blocks consumed from p) mod 4:
+            // bit 0 = which of its 2 slots, bit 1 = that slot's phase parity
+            uint32_t use = 0;
             int sb = 0;
             uint32_t pb = 0;
             int i = 0;
@@ -413,9 +415,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                 tc_fence_after();
                 int p = 0;          // producer of node block kb = kb % np
                 for (int kb = 0; kb < nkb; ++kb) {
-                    const int u = use[p];
-                    const int sa = p * SP + (u & (SP - 1));
-                    const uint32_t pa = (uint32_t)((u / SP) & 1);
+                    const uint32_t v = (use >> (2 * p)) & 3u;
+                    const int sa = p * SP + (int)(v & 1u);
+                    const uint32_t pa = v >> 1;
 #ifdef MF_TRACE
                     long long _t = clock64();
 #endif
@@ -438,7 +440,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                     mma_commit(emptyB + sb);
                     mma_commit_mc(emptyA + sa, (uint16_t)(1u << p));   // slot read: tell its producer
                     if (p != rank) mbar_expect_tx(fullA + sa, abytes);   // arm the slot's next fill
-                    use[p] = u + 1;
+                    use = (use & ~(3u << (2 * p))) | (((v + 1u) & 3u) << (2 * p));
                     if (++sb == SB) { sb = 0; pb ^= 1; }
                     if (++p == np) p = 0;
                 }
@@ -462,6 +464,8 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
         uint32_t aoff[RPT];
 #pragma unroll
         for (int j = 0; j < RPT; ++j) aoff[j] = a_off(rg + RS * j, c);
+        // scratch slot `lane` holds node nperm of the block: slot e*CPR + c = node c*8 + e
+        const int nperm = (lane % CPR) * 8 + lane / CPR;
         int u = 0;              // node blocks produced by this CTA so far
         int sbuf = 0;           // node scratch buffer (double-buffered)
         bool ok = true;
@@ -471,7 +475,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
             int kn = rank;
 #pragma unroll
             for (int dd = 0; dd < kNodeAhead; ++dd) {
-                yq[dd] = ldg_keep(args.nodes_s + (kn < nkb ? kn : 0) * kKB + lane);
+                yq[dd] = ldg_keep(args.nodes_s + (kn < nkb ? kn : 0) * kKB + nperm);
                 kn += np;
                 if (kn >= nkb) kn = rank;
             }
@@ -504,7 +508,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                 const float4 ycur = yq[0];
 #pragma unroll
                 for (int dd = 0; dd < kNodeAhead - 1; ++dd) yq[dd] = yq[dd + 1];
-                yq[kNodeAhead - 1] = ldg_keep(args.nodes_s + kfetch * kKB + lane);
+                yq[kNodeAhead - 1] = ldg_keep(args.nodes_s + kfetch * kKB + nperm);
                 kfetch += np;
                 if (kfetch >= nkb) kfetch = rank;
                 float4 *scr = sN + ((warp - 2) * 2 + sbuf) * kKB;
@@ -518,7 +522,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                 for (int e = 0; e < 8; ++e) {
                     const int n = n0 + e;
                     if (full || n < args.N) {
-                        const float4 y = scr[c * 8 + e];
+                        const float4 y = scr[e * CPR + c];   // node c*8+e (conflict-free broadcast)
                         const float2 ny0 = make_float2(y.x, y.x), ny1 = make_float2(y.y, y.y);
                         const float2 ny2 = make_float2(y.z, y.z), ny3 = make_float2(y.w, y.w);
 #pragma unroll
@@ -568,7 +572,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                 const long long _t = clock64();
                 if (pt == 0) TRACE_ADD(14, (unsigned long long)(_t - _tp));
 #endif
-                const bool got = mbar_wait(emptyA + sa, pa ^ 1, epi.err, 6, kb);
+                bool got = true;
+                if (lane == 0) got = mbar_wait(emptyA + sa, pa ^ 1, epi.err, 6, kb);
+                got = __shfl_sync(0xffffffffu, got, 0);
                 if (pt == 0) TRACE_ADD(5, (unsigned long long)(clock64() - _t));
                 uint8_t *base = sA + sa * abytes;
                 if (got) {
