@@ -71,6 +71,9 @@ def lib():
             L.oracle_loglike.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, fp, fp,
                                          ctypes.c_int, dp, ctypes.c_int]
             L.oracle_loglike.restype = ctypes.c_int
+            L.oracle_loglike_columns.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, fp,
+                                                 ctypes.c_int, dp, ctypes.c_int]
+            L.oracle_loglike_columns.restype = ctypes.c_int
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -245,6 +248,20 @@ class Model:
                              ex.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                              ex.shape[1], _dp(out), nthreads)
         return out
+
+
+def loglike_columns(model: "Model", F, extrinsic, nthreads: int = 0):
+    """lnL [Q] from given interpolated columns F [Q,K] (node_values order)
+    and FP32 extrinsic [Q,5]: the time interpolation, amplitudes and
+    quadratic form of Model.loglike without the RBF evaluation."""
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    ex = np.ascontiguousarray(extrinsic, dtype=np.float32)
+    assert F.shape == (ex.shape[0], model.K)
+    out = np.empty(ex.shape[0])
+    lib().oracle_loglike_columns(ctypes.byref(model._c), ex.shape[0], _dp(F),
+                                 ex.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                 ex.shape[1], _dp(out), nthreads)
+    return out
 
 
 def num_threads() -> int:

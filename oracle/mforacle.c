@@ -188,13 +188,11 @@ static int col_sigma0(const oracle_model *m, int k) {
     return m->n_det * m->n_modes * 2 * m->rank + k * m->n_modes * m->n_modes;
 }
 
-/* Full lnL for one query.  Returns 0, or 1 when the spline stencil leaves
- * the sampled time window (then *out = NaN). */
-static int loglike_point(const oracle_model *m, const double *theta, const double *ext,
-                         double *f, double *out) {
-    double x[4];
-    rotate(m, theta, x);
-    rbf_eval_point(m, x, f);
+/* lnL of one query from its interpolated columns f[K] (node_values order):
+ * time interpolation, amplitudes and Eq. logl_complete.  Returns 0, or 1
+ * when the spline stencil leaves the sampled time window (then *out = NaN). */
+static int loglike_from_columns(const oracle_model *m, const double *f, const double *ext,
+                                double *out) {
     const int nm = m->n_modes, S = m->stencil, half = S / 2 - 1;
     double c_re[8], c_im[8], ys_re[32], ys_im[32];
     double lnl = 0.0;
@@ -267,9 +265,32 @@ int oracle_loglike(const oracle_model *m, int Q, const float *intrinsic, const f
             double th[4], ex[5];
             for (int i = 0; i < 4; ++i) th[i] = (double)intrinsic[(size_t)q * 4 + i];
             for (int i = 0; i < 5; ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
-            bad += loglike_point(m, th, ex, f, out + q);
+            double x[4];
+            rotate(m, th, x);
+            rbf_eval_point(m, x, f);
+            bad += loglike_from_columns(m, f, ex, out + q);
         }
         free(f);
+    }
+    return bad;
+}
+
+/* lnL for Q queries whose interpolated columns are given: F [Q][K] in the
+ * node_values column order (e.g. a surrogate's prediction), extrinsic as in
+ * oracle_loglike.  Returns the number of out-of-window queries. */
+int oracle_loglike_columns(const oracle_model *m, int Q, const double *F, const float *extrinsic,
+                           int E, double *out, int nthreads) {
+    int bad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    #pragma omp parallel for reduction(+:bad) schedule(dynamic, 8)
+    for (int q = 0; q < Q; ++q) {
+        double ex[5];
+        for (int i = 0; i < 5; ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
+        bad += loglike_from_columns(m, F + (size_t)q * m->K, ex, out + q);
     }
     return bad;
 }
