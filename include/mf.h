@@ -161,7 +161,8 @@ MF_API int mf_set_form(mf_handle *h, mf_form form);
  *                   - 1/2 sum_mu,nu conj(c_k,mu) sigma_k,mu,nu c_k,nu ],
  *   c_k,mu = (d_ref/d_L) 1/2 [ (F+ + i Fx) Y_{l,-m} + (-1)^l (F+ - i Fx) conj(Y_{l,m}) ],
  *   Y = -2Y_lm(iota, phi_c).
- * intrinsic : device [Q][4] FP32, sampler-frame coordinates.
+ * intrinsic : device [Q][4] FP32, sampler-frame coordinates; 16-byte aligned
+ *             (rows are read as float4), else MF_E_INVAL.
  * extrinsic : device [Q][E] FP32, E >= 5, columns (d_L [Mpc], cos iota,
  *             psi, phi_c, t_c [s]).
  * out_lnL   : device [Q] FP32, written by the call.
@@ -198,13 +199,88 @@ MF_API int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const float 
  */
 MF_API int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched events: many interpolants (events, e.g. independent sampler runs
+ * with their own nodes, SVD rank and batch size) evaluated by ONE persistent
+ * tcgen05 launch (plus one combine launch), replayed from a CUDA graph.  The
+ * per-query result of every event is exactly mf_loglike's (Eq.
+ * logl_complete); only the scheduling differs.
+ *
+ * mf_batch_create plans a batch over `n_events` (1..128) handles that share
+ * one tcgen05 form (MF_FORM_BF16 .. MF_FORM_FP16_3TERM, set beforehand) and
+ * the same number of modes; layout, basis and detectors must be set.
+ *   Q_plan[e]      : host, the batch size expected for event e (shapes the
+ *                    timing runs; calls may use any sizes).
+ *   autotune_shape : 1 = time every launch shape that fits (passes per event
+ *                    = cluster size, weight-ring depth) on synthetic queries
+ *                    of the planned sizes and keep the fastest; 0 = fewest
+ *                    passes, deepest ring, no timing.
+ * The plan re-lays out every handle in the chosen number of column passes
+ * (the "pass_count" option of mf_set_option, which mf_loglike honours too).
+ * The batch keeps pointers to the handles: free the batch before them.
+ * Changing a handle's form, layout, basis, detectors, rotation or pass
+ * options afterwards makes mf_batch_loglike return MF_E_STATE.
+ * Errors: MF_E_INVAL (arguments, mixed forms or mode counts), MF_E_STATE
+ * (a handle not ready or not in a tcgen05 form), MF_E_NOTIMPL (no shape
+ * fits), MF_E_TIMEOUT (a timing run's bounded wait gave up).  On error the
+ * handles get their previous layout back and *out is NULL. */
+typedef struct mf_batch mf_batch;
+MF_API int mf_batch_create(mf_handle *const *hs, int n_events, const int *Q_plan,
+                           int autotune_shape, void *stream, mf_batch **out);
+
+/* Enqueue lnL for every event of the batch on `stream` (asynchronous).
+ * intrinsic[e] / extrinsic[e] / out_lnL[e]: device pointers as in
+ * mf_loglike for event e, Q[e] queries (0 allowed, then the pointers may be
+ * NULL), E >= 5 the extrinsic row stride of all events, sum of Q <= 2^30.
+ * The first call, and any call whose pointers or sizes differ from the
+ * previous call's, captures the launches into the batch's CUDA graph
+ * (updating it in place); an identical call replays it.  A call with larger
+ * sizes than any before grows a scratch buffer and synchronises `stream`
+ * first.  Out-of-window queries get NaN as in mf_loglike; the counts and
+ * device status are read with mf_batch_sync_status. */
+MF_API int mf_batch_loglike(mf_batch *b, const float *const *intrinsic,
+                            const float *const *extrinsic, const int *Q, int E,
+                            float *const *out_lnL, void *stream);
+
+/* "timing": 1 = CUDA events around each mf_batch_loglike (read with
+ * mf_batch_query "kernel_ms"); "graph": 0 = launch directly, 1 (default) =
+ * capture / replay. */
+MF_API int mf_batch_set_option(mf_batch *b, const char *key, double value);
+
+/* "n_events", "n_pass" (passes per event = cluster size), "ring" (weight
+ * ring depth), "nbox" (widest pass), "clusters" (resident clusters
+ * launched), "n_items" (work items of the last call), "captures",
+ * "replays", "launches" (kernel launches per call), "n_tuned" (shapes timed
+ * by the autotuner), "kernel_ms" (last call, "timing" on; waits for it). */
+MF_API int mf_batch_query(const mf_batch *b, const char *key, double *value);
+
+/* The autotuner's i-th timed shape and its time (ms) per batch launch. */
+MF_API int mf_batch_tuning(const mf_batch *b, int i, int *n_pass, int *ring, double *ms);
+
+/* Wait for `stream`; MF_E_TIMEOUT if a bounded device wait gave up, else
+ * MF_E_RANGE with *n_bad = out-of-window queries over all events, else
+ * MF_OK.  Resets the counters. */
+MF_API int mf_batch_sync_status(mf_batch *b, void *stream, long long *n_bad);
+
+MF_API void mf_batch_free(mf_batch *b);
+
+/* One-shot convenience: plan (no timing), run, wait for `stream`, free. */
+MF_API int mf_loglike_batch(mf_handle *const *hs, int n_events, const float *const *intrinsic,
+                            const float *const *extrinsic, const int *Q, int E,
+                            float *const *out_lnL, void *stream);
+
 /* Tuning / instrumentation knobs (host-side, take effect at the next call):
  *   "timing"   : 1 = record CUDA events around the main lnL kernel of each
  *                mf_loglike (read back with mf_query "kernel_ms"), 0 = off.
  *   "pass_max" : widest column pass (16..512, multiple of 16) the tcgen05
  *                forms may use; re-lays out the weights.
  *   "tc_nbs"   : depth (2..4) of the weight-tile ring of the tcgen05 kernel;
- *                0 (default) = deepest that fits in shared memory. */
+ *                0 (default) = deepest that fits in shared memory.
+ *   "pass_count": 0 (default) = as few column passes as "pass_max" allows;
+ *                1..8 = exactly this many for the tcgen05 forms (contiguous
+ *                groups, widest pass minimised; the FP32 form keeps its own
+ *                rule); re-lays out the weights, MF_E_INVAL if they do not
+ *                fit (the previous layout is kept). */
 MF_API int mf_set_option(mf_handle *h, const char *key, double value);
 
 /* Wait for `stream`, then report device-side status accumulated since the

@@ -14,8 +14,8 @@ import numpy as np
 
 from .build import SO as _SO_PATH, build
 
-__all__ = ["build", "lib", "MFError", "Interpolant", "svd_compress", "FORMS",
-           "pack_node_values"]
+__all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch",
+           "svd_compress", "FORMS", "pack_node_values"]
 
 MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
 MF_E_ILLCOND, MF_E_RANGE, MF_E_TIMEOUT, MF_E_NOTIMPL, MF_E_STATE = -4, -5, -6, -7, -8
@@ -59,6 +59,16 @@ def lib():
         L.mf_loglike_noalloc.argtypes = [vp, vp, vp, ip, ip, vp, vp]
         L.mf_free.argtypes = [vp]
         L.mf_free.restype = None
+        L.mf_batch_create.argtypes = [vp, ip, vp, ip, vp, ctypes.POINTER(vp)]
+        L.mf_batch_loglike.argtypes = [vp, vp, vp, vp, ip, vp, vp]
+        L.mf_batch_set_option.argtypes = [vp, ctypes.c_char_p, dp]
+        L.mf_batch_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
+        L.mf_batch_tuning.argtypes = [vp, ip, ctypes.POINTER(ip), ctypes.POINTER(ip),
+                                      ctypes.POINTER(dp)]
+        L.mf_batch_sync_status.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.mf_batch_free.argtypes = [vp]
+        L.mf_batch_free.restype = None
+        L.mf_loglike_batch.argtypes = [vp, ip, vp, vp, vp, ip, vp, vp]
         _lib = L
     return _lib
 
@@ -236,3 +246,108 @@ class Interpolant:
             self.close()
         except Exception:
             pass
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*ptrs)
+    return arr
+
+
+def _batch_args(intrinsic, extrinsic, out):
+    import torch
+    n = len(intrinsic)
+    assert len(extrinsic) == n and len(out) == n
+    Q = (ctypes.c_int * n)()
+    E = None
+    pi, pe, po = [], [], []
+    for e in range(n):
+        th, ex, o = intrinsic[e], extrinsic[e], out[e]
+        for t in (th, ex, o):
+            assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        q = ex.shape[0]
+        assert th.shape == (q, 4) and o.shape == (q,)
+        if E is None:
+            E = ex.shape[1]
+        assert ex.shape[1] == E, "all events share the extrinsic row stride"
+        Q[e] = q
+        pi.append(th.data_ptr() if q else None)
+        pe.append(ex.data_ptr() if q else None)
+        po.append(o.data_ptr() if q else None)
+    return _ptr_array(pi), _ptr_array(pe), Q, (E if E is not None else 5), _ptr_array(po)
+
+
+class Batch:
+    """Owns an mf_batch: many Interpolants (same tcgen05 form and mode
+    count) evaluated by one persistent launch replayed from a CUDA graph.
+    Keep the Interpolants alive while the Batch exists."""
+
+    def __init__(self, interpolants, Q_plan, autotune=True, stream=None):
+        self.members = list(interpolants)
+        n = len(self.members)
+        hs = _ptr_array([m._h.value for m in self.members])
+        qp = (ctypes.c_int * n)(*[int(q) for q in Q_plan])
+        b = ctypes.c_void_p()
+        _check(lib().mf_batch_create(hs, n, qp, int(bool(autotune)),
+                                     _stream_ptr(stream), ctypes.byref(b)), "mf_batch_create")
+        self._b = b
+
+    def loglike(self, intrinsic, extrinsic, out=None, stream=None):
+        """lnL of every event: lists of device tensors intrinsic[e] [Q_e,4],
+        extrinsic[e] [Q_e,E]; returns (or fills) the list out[e] [Q_e]."""
+        import torch
+        if out is None:
+            out = [torch.empty(x.shape[0], dtype=torch.float32, device=x.device) for x in extrinsic]
+        pi, pe, Q, E, po = _batch_args(intrinsic, extrinsic, out)
+        _check(lib().mf_batch_loglike(self._b, pi, pe, Q, E, po, _stream_ptr(stream)),
+               "mf_batch_loglike")
+        return out
+
+    def set_option(self, key, value):
+        _check(lib().mf_batch_set_option(self._b, key.encode(), float(value)),
+               f"mf_batch_set_option({key})")
+
+    def query(self, key):
+        v = ctypes.c_double()
+        _check(lib().mf_batch_query(self._b, key.encode(), ctypes.byref(v)),
+               f"mf_batch_query({key})")
+        return v.value
+
+    def tuning(self):
+        """[(n_pass, ring, ms)] of every shape the autotuner timed."""
+        out = []
+        for i in range(int(self.query("n_tuned"))):
+            a, b, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+            _check(lib().mf_batch_tuning(self._b, i, ctypes.byref(a), ctypes.byref(b),
+                                         ctypes.byref(ms)), "mf_batch_tuning")
+            out.append((a.value, b.value, ms.value))
+        return out
+
+    def sync_status(self, stream=None):
+        n = ctypes.c_longlong()
+        rc = lib().mf_batch_sync_status(self._b, _stream_ptr(stream), ctypes.byref(n))
+        if rc not in (MF_OK, MF_E_RANGE):
+            raise MFError(rc, "mf_batch_sync_status")
+        return rc, n.value
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().mf_batch_free(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def loglike_batch(interpolants, intrinsic, extrinsic, out=None, stream=None):
+    """One-shot mf_loglike_batch (untimed plan, one launch, waits)."""
+    import torch
+    if out is None:
+        out = [torch.empty(x.shape[0], dtype=torch.float32, device=x.device) for x in extrinsic]
+    hs = _ptr_array([m._h.value for m in interpolants])
+    pi, pe, Q, E, po = _batch_args(intrinsic, extrinsic, out)
+    _check(lib().mf_loglike_batch(hs, len(interpolants), pi, pe, Q, E, po, _stream_ptr(stream)),
+           "mf_loglike_batch")
+    return out

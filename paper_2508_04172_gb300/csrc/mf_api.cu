@@ -22,8 +22,6 @@ bool supported_mode(int l, int m) {
     return (l == 2 && (m == 2 || m == 1)) || (l == 3 && (m == 3 || m == 2)) || (l == 4 && m == 4);
 }
 
-bool is_tc_form(mf_form f) { return f != MF_FORM_FP32; }
-
 __global__ void convert_fp32_kernel(const double *__restrict__ W64, int rows, int K,
                                     const int *__restrict__ user_of_dev, int Kdev, int Nk,
                                     float *__restrict__ W32) {
@@ -63,6 +61,37 @@ void free_form(mf_handle *h) {
 
 namespace mf {
 
+bool is_tc_form(mf_form f) { return f != MF_FORM_FP32; }
+
+// Split group widths w[0..n) into exactly `count` contiguous non-empty runs
+// minimising the widest run (each padded to kPassAlign); start[c] = first
+// group of run c.  Returns the widest padded run, or -1 if count > n.
+static int split_exact(const std::vector<int> &w, int count, std::vector<int> &start) {
+    const int n = (int)w.size();
+    if (count < 1 || count > n) return -1;
+    auto up = [](int x) { return (x + kPassAlign - 1) / kPassAlign * kPassAlign; };
+    std::vector<int> pre(n + 1, 0);
+    for (int i = 0; i < n; ++i) pre[i + 1] = pre[i] + w[i];
+    const int INF = 1 << 30;
+    // best[c][i]: widest run when groups [0, i) form c runs; cut[c][i]: start of the last run
+    std::vector<std::vector<int>> best(count + 1, std::vector<int>(n + 1, INF)),
+        cut(count + 1, std::vector<int>(n + 1, 0));
+    best[0][0] = 0;
+    for (int c = 1; c <= count; ++c)
+        for (int i = c; i <= n; ++i)
+            for (int j = c - 1; j < i; ++j) {
+                if (best[c - 1][j] == INF) continue;
+                int v = std::max(best[c - 1][j], up(pre[i] - pre[j]));
+                if (v < best[c][i]) { best[c][i] = v; cut[c][i] = j; }
+            }
+    start.assign(count, 0);
+    for (int c = count, i = n; c >= 1; --c) {
+        start[c - 1] = cut[c][i];
+        i = cut[c][i];
+    }
+    return best[count][n];
+}
+
 // Device column layout: per detector, its overlap groups (interleaved Re/Im
 // of the rank coefficients, padded to 8) then its cross-term group; groups
 // are packed into passes of at most pass_max columns (each padded to 16).
@@ -81,12 +110,28 @@ int build_layout(mf_handle *h) {
     const int pmax = std::max(h->pass_max, up(gmax, kPassAlign));
     const int npass_min = (total + pmax - 1) / pmax;
     const int target = (total + npass_min - 1) / npass_min;
+    // exact pass count requested: contiguous min-max split of the groups
+    std::vector<int> cut_at;
+    if (h->pass_count > 0) {
+        std::vector<int> w;
+        for (auto &g : gs) w.push_back(g.width);
+        int widest = split_exact(w, h->pass_count, cut_at);
+        if (widest < 0 || widest > pmax) return MF_E_INVAL;
+    }
     h->groups.clear();
     h->passes.clear();
     Pass cur{0, 0, 0, 0};
     int col = 0;
+    size_t next_cut = 1;
     for (size_t i = 0; i < gs.size(); ++i) {
-        if (cur.ng > 0 && (cur.width + gs[i].width > pmax || cur.width >= target)) {
+        bool split;
+        if (!cut_at.empty()) {
+            split = next_cut < cut_at.size() && (int)i == cut_at[next_cut];
+            if (split) ++next_cut;
+        } else {
+            split = cur.ng > 0 && (cur.width + gs[i].width > pmax || cur.width >= target);
+        }
+        if (split) {
             cur.width = up(cur.width, kPassAlign);
             h->passes.push_back(cur);
             col += cur.width;
@@ -171,6 +216,7 @@ int prepare_form(mf_handle *h, mf_form f) {
     if (!h->have_layout) return MF_E_STATE;
     free_form(h);
     h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : 176;
+    h->pass_count = is_tc_form(f) ? h->pass_count_user : 0;   // exact counts: tcgen05 forms only
     int rc = build_layout(h);
     if (rc) return rc;
     MF_CUDA(cudaMalloc((void **)&h->d_user_of_dev, sizeof(int) * h->Kdev));
@@ -196,6 +242,7 @@ int prepare_form(mf_handle *h, mf_form f) {
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaDeviceSynchronize());
     h->form = f;
+    ++h->gen;
     return MF_OK;
 }
 
@@ -298,6 +345,7 @@ int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, double dt)
     h->t0 = t0;
     h->dt = dt;
     h->have_basis = true;
+    ++h->gen;
     return MF_OK;
 }
 
@@ -307,6 +355,7 @@ int mf_set_detectors(mf_handle *h, const double *det, double d_ref) {
     h->det.assign(det, det + 3 * h->n_det);
     h->d_ref = d_ref;
     h->have_det = true;
+    ++h->gen;
     return MF_OK;
 }
 
@@ -321,6 +370,7 @@ int mf_set_rotation(mf_handle *h, const double *metric, const double *centre) {
         for (int i = 0; i < 16; ++i) h->R[i] = (i % 5 == 0) ? 1.0 : 0.0;
     }
     for (int i = 0; i < 4; ++i) h->centre[i] = centre ? centre[i] : 0.0;
+    ++h->gen;
     return MF_OK;
 }
 
@@ -333,6 +383,8 @@ int mf_set_form(mf_handle *h, mf_form f) {
     if (f == h->form && (h->d_W32 || h->d_Whi)) return MF_OK;
     return mf::prepare_form(h, f);
 }
+
+static const int kMaxPassCount = 8;
 
 static int ensure_partial(mf_handle *h, size_t need) {
     if (need <= h->partial_cap) return MF_OK;
@@ -349,6 +401,7 @@ int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int
     if (!h || Q < 0 || Q > (1 << 26) || E < 5) return MF_E_INVAL;
     if (Q == 0) return MF_OK;
     if (!intrinsic || !extrinsic || !out_lnL) return MF_E_INVAL;
+    if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;   // rows are read as float4
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
     cudaStream_t st = (cudaStream_t)stream;
     const int np = (int)h->passes.size();
@@ -359,7 +412,7 @@ int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int
         partial = h->d_partial;
     }
     if (h->timing) MF_CUDA(cudaEventRecord(h->ev0, st));
-    int rc = is_tc_form(h->form) ? mf::launch_tc(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial)
+    int rc = mf::is_tc_form(h->form) ? mf::launch_tc(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial)
                                  : mf::launch_fp32(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial);
     if (rc) return rc;
     if (h->timing) MF_CUDA(cudaEventRecord(h->ev1, st));
@@ -371,6 +424,7 @@ int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *out, voi
     if (!h || Q < 0 || Q > (1 << 26)) return MF_E_INVAL;
     if (Q == 0) return MF_OK;
     if (!intrinsic || !out) return MF_E_INVAL;
+    if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;
     if (!h->have_layout) return MF_E_STATE;
     if (h->form != MF_FORM_FP32) return MF_E_NOTIMPL;
     return mf::launch_fp32_columns(h, intrinsic, Q, out, (cudaStream_t)stream);
@@ -391,7 +445,22 @@ int mf_set_option(mf_handle *h, const char *key, double value) {
         int v = (int)value;
         if (v < 16 || v > 512 || v % 16) return MF_E_INVAL;
         h->pass_max_user = v;
-        if (h->have_layout && is_tc_form(h->form)) return mf::prepare_form(h, h->form);
+        if (h->have_layout && mf::is_tc_form(h->form)) return mf::prepare_form(h, h->form);
+        return MF_OK;
+    }
+    if (k == "pass_count") {
+        int v = (int)value;
+        if (v < 0 || v > kMaxPassCount || v != value) return MF_E_INVAL;
+        const int old = h->pass_count_user;
+        h->pass_count_user = v;
+        if (h->have_layout && (h->d_W32 || h->d_Whi)) {
+            int rc = mf::prepare_form(h, h->form);
+            if (rc) {   // keep the previous, still valid layout
+                h->pass_count_user = old;
+                mf::prepare_form(h, h->form);
+                return rc;
+            }
+        }
         return MF_OK;
     }
     if (k == "tc_nbs") {

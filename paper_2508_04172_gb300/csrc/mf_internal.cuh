@@ -1,6 +1,7 @@
 // Internal definitions shared by the libmf translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -66,6 +67,37 @@ struct RotParams {
     float pre;               // eps * sqrt(log2 e): exp(-(eps r)^2) = exp2(-|pre (x - y)|^2)
 };
 
+// One interpolant as the tcgen05 kernel sees it: everything that does not
+// change from call to call.  Passed by value (one event) or as a device
+// array (batched launch).
+struct TcEvent {
+    CUtensorMap tm_hi, tm_lo;   // W_hi / W_lo [Kdev][Nk] K-major, box kKB x nbox
+    EpiParams epi;
+    RotParams rot;
+    const float4 *nodes_s;      // [Nk] nodes * (-pre), padding zero
+    const float *colscale;      // [Kdev] per-column scale (FP16 forms) or nullptr
+    int N, P;                   // nodes, tail monomials
+    int nkb;                    // node blocks of 32 (Nk / 32)
+    int nbox;                   // rows of one W tile = widest pass of this event
+};
+
+// Per-call arguments of a batched launch (kernel parameter; < 32 KB).
+constexpr int kMaxBatch = 128;
+struct TcBatchCall {
+    int n_ev, n_items, E, np;    // events, work items, extrinsic stride, passes (= cluster size)
+    int n_clusters, sb, nbox_max;
+    unsigned *err;               // device status words of the batch
+    int order[kMaxBatch];        // events by decreasing cost per tile
+    int tprefix[kMaxBatch + 1];  // first work item of order[k]
+    int qprefix[kMaxBatch + 1];  // first query of event e (event order)
+    int Q[kMaxBatch];
+    const float *intr[kMaxBatch];
+    const float *ext[kMaxBatch];
+    float *out[kMaxBatch];
+    float *partial[kMaxBatch];   // [np][Q] per event (np > 1)
+    unsigned long long *bad[kMaxBatch];
+};
+
 }  // namespace mf
 
 struct mf_handle {
@@ -111,6 +143,9 @@ struct mf_handle {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int tc_nbs = 0;                 // W ring depth of the tcgen05 kernel (0: automatic)
     int pass_max_user = 0;          // 0: form default
+    int pass_count_user = 0;        // 0: as few passes as pass_max allows; else exactly this many
+    int pass_count = 0;             // the value the current layout was built with (tcgen05 forms)
+    unsigned gen = 0;               // bumped whenever the device layout or weights change
     // tcgen05 forms: tensor maps (opaque 128-byte CUtensorMap) of W_hi / W_lo
     alignas(64) unsigned char tmap_hi[128];
     alignas(64) unsigned char tmap_lo[128];
@@ -140,6 +175,13 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
               cudaStream_t st, float *partial);
 int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStream_t st,
                    unsigned long long *bad);
+// batched tcgen05 launch (all events share form and mode count)
+int fill_tc_event(const mf_handle *h, TcEvent *out);
+size_t tc_smem_bytes(mf_form f, int np, int nbox_max, int sb);   // 0: does not fit
+int tc_batch_max_clusters(mf_form f, int n_modes, int np, int nbox_max, int sb, int *max_clusters);
+int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBatchCall &bc,
+                    cudaStream_t st);
+bool is_tc_form(mf_form f);
 }  // namespace mf
 
 #define MF_CUDA(call)                                                              \

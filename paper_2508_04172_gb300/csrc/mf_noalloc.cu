@@ -62,6 +62,7 @@ extern "C" int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const fl
     if (!h || Q < 0 || Q > (1 << 26) || E < 5) return MF_E_INVAL;
     if (Q == 0) return MF_OK;
     if (!intrinsic || !extrinsic || !out_lnL) return MF_E_INVAL;
+    if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;   // rows are read as float4
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
     if (h->form != MF_FORM_FP32 || !h->d_W32) return MF_E_STATE;
     const size_t np = h->passes.size();

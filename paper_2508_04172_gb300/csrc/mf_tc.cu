@@ -29,15 +29,6 @@ constexpr int kAccCols = 256;           // TMEM columns per accumulator buffer (
 constexpr int kRowBytes = kKB * 2;      // bytes per A/B row
 constexpr int kATile = kTile * kRowBytes;   // bytes per 16-bit A part
 
-#ifdef MF_TRACE
-// Development timeline: per CTA, 16 globaltimer stamps / accumulated waits.
-__device__ unsigned long long g_trace[4096 * 16];
-#define TRACE_SET(i, v) g_trace[(blockIdx.y * gridDim.x + blockIdx.x) * 16 + (i)] = (v)
-#define TRACE_ADD(i, v) atomicAdd(&g_trace[(blockIdx.y * gridDim.x + blockIdx.x) * 16 + (i)], (v))
-#else
-#define TRACE_SET(i, v)
-#define TRACE_ADD(i, v)
-#endif
 constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s bound on every mbarrier wait
 constexpr uint32_t kSuspendNs = 20000;          // try_wait suspend-time hint
 
@@ -240,17 +231,67 @@ struct TmemAcc {
     }
 };
 
-struct TcArgs {
+// Per-call pointers and size of one event.
+struct EvIO {
     const float *intr, *ext;
-    int Q, E, N, P, Nk, nbox;
-    const float4 *nodes_s;
-    const float *colscale;  // [Kdev] (FP16 forms: s_c * 2^-14), nullptr for BF16
     float *out, *partial;
-    float phi_log2_scale;   // log2 of the A-operand scale (14 for FP16, 0 for BF16)
-    int n_tiles;            // query tiles of 128
-    int n_clusters;         // clusters launched (each loops over tiles)
-    int sb;                 // W ring depth
+    int Q;
 };
+
+// Per-call arguments of the single-event launch.
+struct TcCall {
+    const float *intr, *ext;
+    float *out, *partial;
+    int Q, E;
+    int n_tiles;            // query tiles of 128
+    int n_clusters;         // clusters launched (each loops over work items)
+    int sb;                 // W ring depth
+    int nbox_max;           // W ring slot rows
+    unsigned *err;          // device status words
+};
+
+// Work source of the single-event kernel: work item = query tile.
+struct SingleSrc {
+    const TcEvent *ev;
+    const TcCall *c;
+    __device__ __forceinline__ int n_items() const { return c->n_tiles; }
+    __device__ __forceinline__ void item(int it, int &e, int &tile) const {
+        e = 0;
+        tile = it;
+    }
+    __device__ __forceinline__ const TcEvent &event(int) const { return *ev; }
+    __device__ __forceinline__ EvIO io(int) const { return EvIO{c->intr, c->ext, c->out, c->partial, c->Q}; }
+};
+
+// Work source of the batched kernel: work items are (event, query tile)
+// pairs; events are listed in order of decreasing cost per tile and the
+// tiles of one event are consecutive.
+struct BatchSrc {
+    const TcEvent *evs;
+    const TcBatchCall *c;
+    __device__ __forceinline__ int n_items() const { return c->n_items; }
+    __device__ __forceinline__ void item(int it, int &e, int &tile) const {
+        int lo = 0, hi = c->n_ev;   // invariant: tprefix[lo] <= it < tprefix[hi]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (c->tprefix[mid] <= it) lo = mid;
+            else hi = mid;
+        }
+        e = c->order[lo];
+        tile = it - c->tprefix[lo];
+    }
+    __device__ __forceinline__ const TcEvent &event(int e) const { return evs[e]; }
+    __device__ __forceinline__ EvIO io(int e) const {
+        return EvIO{c->intr[e], c->ext[e], c->out[e], c->partial[e], c->Q[e]};
+    }
+};
+
+// Work item handled by cluster `cid` in round r: snake order (forward in
+// even rounds, backward in odd ones), so that with items sorted by
+// decreasing cost the clusters' totals stay close.
+__device__ __forceinline__ int item_of(int r, int cid, int nc) {
+    return r * nc + ((r & 1) ? nc - 1 - cid : cid);
+}
 
 // A-operand byte offset of (row r, 16-byte chunk c) in a swizzled tile: the
 // chunk index is XORed with address bits [7, 7 + log2(kSwz/16)).
@@ -267,17 +308,44 @@ __device__ __forceinline__ void rotate_row(const RotParams &rot, const float *in
         xu[i] = rot.R[4 * i] * d[0] + rot.R[4 * i + 1] * d[1] + rot.R[4 * i + 2] * d[2] + rot.R[4 * i + 3] * d[3];
 }
 
-// Persistent, warp-specialised kernel, one CTA per SM.  A thread-block cluster
-// of n_pass CTAs (rank = column pass) walks over query tiles (tile = cluster
-// index + i * clusters); every CTA accumulates its pass's columns for the
-// tile, and the RBF tile Phi of node block kb is generated only once, by the
-// CTA of rank kb % n_pass, which copies it into the other CTAs' shared memory
-// with bulk DSMEM copies.
+// Position of a producer warp's node prefetch: the node blocks this CTA makes
+// (kb = rank, rank + np, ...) of its cluster's work items, in order.
+struct NodeCursor {
+    int r;                  // round of the current work item
+    int kb, nkb;
+    const float4 *nodes;
+    bool valid;             // false past the cluster's last work item
+};
+
+template <class Src>
+__device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, int cid, int nc, int rank) {
+    while (cu.valid && cu.kb >= cu.nkb) {
+        ++cu.r;
+        const int it = item_of(cu.r, cid, nc);
+        if (it >= src.n_items()) {
+            cu.valid = false;
+            break;
+        }
+        int e, tile;
+        src.item(it, e, tile);
+        const TcEvent &ev = src.event(e);
+        cu.nkb = ev.nkb;
+        cu.nodes = ev.nodes_s;
+        cu.kb = rank;
+    }
+}
+
+// Persistent, warp-specialised kernel body, one CTA per SM.  A thread-block
+// cluster of np CTAs (rank = column pass) walks over work items (a query tile
+// of one event); every CTA accumulates its pass's columns for the tile, and
+// the RBF tile Phi of node block kb is generated only once, by the CTA of
+// rank kb % np, which copies it into the other CTAs' shared memory with bulk
+// DSMEM copies.
 //   warp 0        TMA: W tiles (pass columns x kKB nodes, K-major, swizzled)
 //                 of the 1-2 weight parts into the W ring,
 //   warp 1        TMEM allocation (2 accumulators x 256 columns); one thread
 //                 issues tcgen05.mma kind::f16 (Phi_hi.W_hi [+ Phi_hi.W_lo
-//                 [+ Phi_lo.W_hi]]) per 16-node step into the tile's buffer,
+//                 [+ Phi_lo.W_hi]]) per 16-node step into the item's buffer,
 //   warps 2..9    Phi producers (this CTA's share of the node blocks): 2-4
 //                 rows x 8 nodes per thread; rotation into the metric
 //                 eigenbasis, Gaussian RBF values / tail monomials (Eq.
@@ -286,26 +354,26 @@ __device__ __forceinline__ void rotate_row(const RotParams &rot, const float *in
 //   warps 10..13  epilogue: thread = accumulator row = query; SVD
 //                 reconstruction at each detector delay, amplitudes, cross
 //                 terms of this pass (Eqs. SVD, projected_h_fd, logl_complete)
-//                 while the MMAs of the next tile fill the other accumulator.
+//                 while the MMAs of the next item fill the other accumulator.
 // Each CTA owns kSlotsPerProducer A slots for the node blocks it makes, so
 // every barrier is waited on phase by phase by its waiters.  Every mbarrier
-// wait is bounded and sets a status bit instead of hanging.
-template <int NM, int AT, int TERMS>
-__global__ void __launch_bounds__(kThreads, 1)
-tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-          TcArgs args, RotParams rot, EpiParams epi) {
+// wait is bounded and sets a status bit instead of hanging.  Every event of
+// a batch has exactly np passes.
+template <int NM, int AT, int TERMS, class Src>
+__device__ __forceinline__ void tc_body(const Src &src, const int np, const int nbox_max, const int SB,
+                                        const int nc, const int E, unsigned *err) {
     constexpr int NA = (TERMS == 3) ? 2 : 1;
     constexpr int NB = (TERMS >= 2) ? 2 : 1;
     constexpr int SP = kSlotsPerProducer;
+    // FP16 forms carry Phi * 2^14 (W columns are scaled to match)
+    constexpr float kPhiLog2 = (AT == 0) ? 14.f : 0.f;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int np = epi.n_pass;                  // cluster size
     const int rank = (int)(blockIdx.x % (unsigned)np);   // == %cluster_ctarank
     const int cid = (int)(blockIdx.x / (unsigned)np);
-    const Pass ps = epi.passes[rank];
-    const int btile = args.nbox * kRowBytes;
-    const int SB = args.sb;
+    const int btile = nbox_max * kRowBytes;
     const int nslot = np * SP;
+    const int n_items = src.n_items();
     uint8_t *sA = smem;                                   // [np][SP][NA][kATile]
     uint8_t *sB = sA + nslot * NA * kATile;               // [SB][NB][btile]
     float4 *sN = (float4 *)(sB + SB * NB * btile);        // [kProdWarps][2][kKB] node blocks
@@ -317,7 +385,6 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
     uint32_t *tslot = (uint32_t *)(done + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nkb = args.Nk / kKB;
     const uint32_t tcols = 2 * kAccCols;
     const uint32_t abytes = (uint32_t)(NA * kATile);
 
@@ -353,33 +420,28 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
     cluster_sync();         // all barriers of the cluster exist before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tslot;
-#ifdef MF_TRACE
-    if (threadIdx.x == 0) {
-        unsigned smid;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-        TRACE_SET(0, gtimer_ns());
-        TRACE_SET(10, smid);
-    }
-#endif
 
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------------------ TMA
-            const uint32_t bytes = (uint32_t)(NB * btile);
             int s = 0;              // W ring slot and its phase parity
             uint32_t ph = 0;
             int issued = 0;
             bool ok = true;
-            for (int tile = cid; tile < args.n_tiles && ok; tile += args.n_clusters) {
+            for (int r = 0; ok; ++r) {
+                const int it = item_of(r, cid, nc);
+                if (it >= n_items) break;
+                int e, tile;
+                src.item(it, e, tile);
+                const TcEvent &ev = src.event(e);
+                const int col0 = ev.epi.passes[rank].col0;
+                const uint32_t bytes = (uint32_t)(NB * ev.nbox * kRowBytes);
+                const int nkb = ev.nkb;
                 for (int kb = 0; kb < nkb; ++kb) {
-#ifdef MF_TRACE
-                    const long long _t = clock64();
-#endif
-                    if (!mbar_wait(emptyB + s, ph ^ 1, epi.err, 1, kb)) { ok = false; break; }
-                    TRACE_ADD(1, (unsigned long long)(clock64() - _t));
+                    if (!mbar_wait(emptyB + s, ph ^ 1, err, 1, kb)) { ok = false; break; }
                     mbar_expect_tx(fullB + s, bytes);
-                    tma_load_2d(sB + (s * NB + 0) * btile, &tm_hi, kb * kKB, ps.col0, fullB + s);
-                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &tm_lo, kb * kKB, ps.col0, fullB + s);
+                    tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kb * kKB, col0, fullB + s);
+                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kb * kKB, col0, fullB + s);
                     ++issued;
                     if (++s == SB) { s = 0; ph ^= 1; }
                 }
@@ -387,7 +449,7 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
             // drain: our last copies must have landed before the CTA may exit
             for (int k = 0; k < SB && k < issued; ++k) {
                 if (--s < 0) { s = SB - 1; ph ^= 1; }
-                mbar_wait(fullB + s, ph, epi.err, 2, 0);
+                mbar_wait(fullB + s, ph, err, 2, 0);
             }
         }
     } else if (warp == 1) {
@@ -398,36 +460,29 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
             uint32_t use = 0;
             int sb = 0;
             uint32_t pb = 0;
-            int i = 0;
             bool ok = true;
             const uint64_t dA0 = sdesc(su32(sA)), dB0 = sdesc(su32(sB));
             const uint64_t dAstep = (uint64_t)(abytes >> 4), dBstep = (uint64_t)((NB * btile) >> 4);
             const uint64_t dAlo = (uint64_t)(kATile >> 4), dBlo = (uint64_t)(btile >> 4);
-            const uint32_t id = idesc(AT, ps.width);
-            for (int tile = cid; tile < args.n_tiles && ok; tile += args.n_clusters, ++i) {
+            for (int r = 0, i = 0; ok; ++r, ++i) {
+                const int it = item_of(r, cid, nc);
+                if (it >= n_items) break;
+                int e, tile;
+                src.item(it, e, tile);
+                const TcEvent &ev = src.event(e);
+                const uint32_t id = idesc(AT, ev.epi.passes[rank].width);
+                const int nkb = ev.nkb;
                 const int acc = i & 1;
                 const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
-#ifdef MF_TRACE
-                const long long _te = clock64();
-#endif
-                if (!mbar_wait(tempty + acc, (((uint32_t)i >> 1) & 1) ^ 1, epi.err, 8, i)) break;
-                TRACE_ADD(11, (unsigned long long)(clock64() - _te));
+                if (!mbar_wait(tempty + acc, (((uint32_t)i >> 1) & 1) ^ 1, err, 8, i)) break;
                 tc_fence_after();
                 int p = 0;          // producer of node block kb = kb % np
                 for (int kb = 0; kb < nkb; ++kb) {
                     const uint32_t v = (use >> (2 * p)) & 3u;
                     const int sa = p * SP + (int)(v & 1u);
                     const uint32_t pa = v >> 1;
-#ifdef MF_TRACE
-                    long long _t = clock64();
-#endif
-                    if (!mbar_wait(fullA + sa, pa, epi.err, 3, kb)) { ok = false; break; }
-                    TRACE_ADD(2, (unsigned long long)(clock64() - _t));
-#ifdef MF_TRACE
-                    _t = clock64();
-#endif
-                    if (!mbar_wait(fullB + sb, pb, epi.err, 4, kb)) { ok = false; break; }
-                    TRACE_ADD(3, (unsigned long long)(clock64() - _t));
+                    if (!mbar_wait(fullA + sa, pa, err, 3, kb)) { ok = false; break; }
+                    if (!mbar_wait(fullB + sb, pb, err, 4, kb)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t a = dA0 + (uint64_t)sa * dAstep, b = dB0 + (uint64_t)sb * dBstep;
 #pragma unroll
@@ -446,10 +501,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                 }
                 mma_commit(tfull + acc);
             }
-            TRACE_SET(4, gtimer_ns());
             // every MMA this thread issued must be complete before TMEM is freed
             mma_commit(done);
-            mbar_wait(done, 0, epi.err, 5, 0);
+            mbar_wait(done, 0, err, 5, 0);
         }
     } else if (warp < 2 + kProdWarps) {
         // --------------------------------------------------- Phi producers
@@ -458,9 +512,8 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
         constexpr int RPT = kTile / RS;             // rows per thread (2 or 4)
         const int pt = threadIdx.x - 64;            // 0..255
         const int c = pt % CPR, rg = pt / CPR;      // chunk (8 nodes); rows rg + RS j
-        const float sc = args.phi_log2_scale;
-        const float2 nsc = make_float2(-sc, -sc);
-        const float tsc = exp2f(sc);
+        const float2 nsc = make_float2(-kPhiLog2, -kPhiLog2);
+        const float tsc = exp2f(kPhiLog2);
         uint32_t aoff[RPT];
 #pragma unroll
         for (int j = 0; j < RPT; ++j) aoff[j] = a_off(rg + RS * j, c);
@@ -471,58 +524,62 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
         bool ok = true;
         // this lane's node of the next kNodeAhead node blocks of this CTA (FIFO)
         float4 yq[kNodeAhead];
-        {
-            int kn = rank;
+        NodeCursor cu{-1, 0, 0, nullptr, true};
+        cursor_settle(cu, src, cid, nc, rank);
 #pragma unroll
-            for (int dd = 0; dd < kNodeAhead; ++dd) {
-                yq[dd] = ldg_keep(args.nodes_s + (kn < nkb ? kn : 0) * kKB + nperm);
-                kn += np;
-                if (kn >= nkb) kn = rank;
-            }
+        for (int dd = 0; dd < kNodeAhead; ++dd) {
+            yq[dd] = cu.valid ? ldg_keep(cu.nodes + cu.kb * kKB + nperm) : make_float4(0.f, 0.f, 0.f, 0.f);
+            cu.kb += np;
+            cursor_settle(cu, src, cid, nc, rank);
         }
-        int kfetch = rank;      // node block whose coordinates enter the FIFO next
-        for (int dd = 0; dd < kNodeAhead; ++dd) { kfetch += np; if (kfetch >= nkb) kfetch = rank; }
-        for (int tile = cid; tile < args.n_tiles && ok; tile += args.n_clusters) {
+        for (int r = 0; ok; ++r) {
+            const int it = item_of(r, cid, nc);
+            if (it >= n_items) break;
+            int e, tile;
+            src.item(it, e, tile);
+            const TcEvent &ev = src.event(e);
+            const EvIO io = src.io(e);
+            const int N = ev.N, P = ev.P, nkb = ev.nkb;
             float2 X[RPT / 2][4];   // row pairs (rg + 2h RS, rg + (2h+1) RS), per coordinate
             float4 xu[RPT];
             {
+                const RotParams &rot = ev.rot;
+                const float pre = rot.pre;
                 float a[RPT][4];
 #pragma unroll
                 for (int j = 0; j < RPT; ++j) {
-                    rotate_row(rot, args.intr, min(tile * kTile + rg + RS * j, args.Q - 1), a[j]);
+                    rotate_row(rot, io.intr, min(tile * kTile + rg + RS * j, io.Q - 1), a[j]);
                     xu[j] = make_float4(a[j][0], a[j][1], a[j][2], a[j][3]);
                 }
 #pragma unroll
                 for (int h2 = 0; h2 < RPT / 2; ++h2)
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        X[h2][k] = make_float2(a[2 * h2][k] * rot.pre, a[2 * h2 + 1][k] * rot.pre);
+                        X[h2][k] = make_float2(a[2 * h2][k] * pre, a[2 * h2 + 1][k] * pre);
             }
             for (int kb = rank; kb < nkb; kb += np) {
-#ifdef MF_TRACE
-                const long long _tp = clock64();
-#endif
                 // node coordinates of this block (pre-negated, pre-scaled): one
                 // coalesced 512-byte load per warp issued kNodeAhead blocks ahead,
                 // shared through the warp's scratch
                 const float4 ycur = yq[0];
 #pragma unroll
                 for (int dd = 0; dd < kNodeAhead - 1; ++dd) yq[dd] = yq[dd + 1];
-                yq[kNodeAhead - 1] = ldg_keep(args.nodes_s + kfetch * kKB + nperm);
-                kfetch += np;
-                if (kfetch >= nkb) kfetch = rank;
+                yq[kNodeAhead - 1] =
+                    cu.valid ? ldg_keep(cu.nodes + cu.kb * kKB + nperm) : make_float4(0.f, 0.f, 0.f, 0.f);
+                cu.kb += np;
+                cursor_settle(cu, src, cid, nc, rank);
                 float4 *scr = sN + ((warp - 2) * 2 + sbuf) * kKB;
                 sbuf ^= 1;
                 scr[lane] = ycur;
                 __syncwarp();
                 const int n0 = kb * kKB + c * 8;
                 float v[RPT][8];   // rows rg + RS j, nodes n0 .. n0+7
-                const bool full = (kb * kKB + kKB <= args.N);
+                const bool full = (kb * kKB + kKB <= N);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int n = n0 + e;
-                    if (full || n < args.N) {
-                        const float4 y = scr[e * CPR + c];   // node c*8+e (conflict-free broadcast)
+                for (int e8 = 0; e8 < 8; ++e8) {
+                    const int n = n0 + e8;
+                    if (full || n < N) {
+                        const float4 y = scr[e8 * CPR + c];   // node c*8+e8 (conflict-free broadcast)
                         const float2 ny0 = make_float2(y.x, y.x), ny1 = make_float2(y.y, y.y);
                         const float2 ny2 = make_float2(y.z, y.z), ny3 = make_float2(y.w, y.w);
 #pragma unroll
@@ -536,16 +593,16 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                             r2 = __ffma2_rn(dd, dd, r2);
                             dd = __fadd2_rn(X[h2][3], ny3);
                             r2 = __ffma2_rn(dd, dd, r2);
-                            v[2 * h2][e] = ex2(-r2.x);
-                            v[2 * h2 + 1][e] = ex2(-r2.y);
+                            v[2 * h2][e8] = ex2(-r2.x);
+                            v[2 * h2 + 1][e8] = ex2(-r2.y);
                         }
                     } else {
                         // tail monomials 1, x1..x4 (times 2^sc), then zero padding
-                        const int q = n - args.N;
+                        const int q = n - N;
 #pragma unroll
                         for (int j = 0; j < RPT; ++j) {
                             float m = (q == 0) ? 1.f : (q == 1) ? xu[j].x : (q == 2) ? xu[j].y : (q == 3) ? xu[j].z : xu[j].w;
-                            v[j][e] = (q < args.P) ? m * tsc : 0.f;
+                            v[j][e8] = (q < P) ? m * tsc : 0.f;
                         }
                     }
                 }
@@ -568,14 +625,9 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                 }
                 const int sa = rank * SP + (u & (SP - 1));
                 const uint32_t pa = (uint32_t)((u / SP) & 1);
-#ifdef MF_TRACE
-                const long long _t = clock64();
-                if (pt == 0) TRACE_ADD(14, (unsigned long long)(_t - _tp));
-#endif
                 bool got = true;
-                if (lane == 0) got = mbar_wait(emptyA + sa, pa ^ 1, epi.err, 6, kb);
+                if (lane == 0) got = mbar_wait(emptyA + sa, pa ^ 1, err, 6, kb);
                 got = __shfl_sync(0xffffffffu, got, 0);
-                if (pt == 0) TRACE_ADD(5, (unsigned long long)(clock64() - _t));
                 uint8_t *base = sA + sa * abytes;
                 if (got) {
 #pragma unroll
@@ -586,84 +638,80 @@ tc_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUt
                     fence_async_smem();
                 }
                 // all producer warps wrote the slot; and all agree whether to go on
-#ifdef MF_TRACE
-                const long long _tb = clock64();
-#endif
                 if (!bar_and_256(got)) { ok = false; break; }
-                if (pt == 0) TRACE_ADD(15, (unsigned long long)(clock64() - _tb));
-#ifdef MF_TRACE
-                const long long _tc2 = clock64();
-#endif
                 if (pt == 0) {
                     // local slot: plain arrive; other CTAs: bulk copy completing
                     // as transaction bytes on their (pre-armed) fullA barrier
-                    const uint32_t src = su32(base), fa = su32(fullA + sa);
+                    const uint32_t src_a = su32(base), fa = su32(fullA + sa);
                     for (int dst = 0; dst < np; ++dst)
-                        if (dst != rank) bulk_copy_to_cta(map_cta(src, dst), src, abytes, map_cta(fa, dst));
+                        if (dst != rank) bulk_copy_to_cta(map_cta(src_a, dst), src_a, abytes, map_cta(fa, dst));
                     mbar_arrive(fullA + sa);
-                    TRACE_ADD(12, 0ull);
                 }
-                if (pt == 0) TRACE_ADD(3, 0ull);
-#ifdef MF_TRACE
-                if (pt == 0) TRACE_ADD(13, 0ull);
-                if (pt == 0) atomicAdd(&g_trace[(blockIdx.y * gridDim.x + blockIdx.x) * 16 + 11], (unsigned long long)(clock64() - _tc2));
-#endif
                 ++u;
             }
         }
-        if (pt == 0) TRACE_SET(6, gtimer_ns());
     } else {
         // ------------------------------------------------------- epilogue
         const int quad = warp & 3;                  // TMEM lane quadrant of this warp
-        const int r = quad * 32 + lane;             // accumulator row == query in tile
-        int i = 0;
-        for (int tile = cid; tile < args.n_tiles; tile += args.n_clusters, ++i) {
+        const int row = quad * 32 + lane;           // accumulator row == query in tile
+        for (int r = 0, i = 0;; ++r, ++i) {
+            const int it = item_of(r, cid, nc);
+            if (it >= n_items) break;
+            int e, tile;
+            src.item(it, e, tile);
+            const TcEvent &ev = src.event(e);
+            const EvIO io = src.io(e);
+            const Pass ps = ev.epi.passes[rank];
             const int acc = i & 1;
-            const int q = tile * kTile + r;
-            const int qc = min(q, args.Q - 1);
-            QueryExt x = load_ext(epi, args.ext, args.E, qc);
-#ifdef MF_TRACE
-            const long long _tw = clock64();
-#endif
-            bool ok = mbar_wait(tfull + acc, ((uint32_t)i >> 1) & 1, epi.err, 7, i);
-            if (r == 0) TRACE_ADD(12, (unsigned long long)(clock64() - _tw));
-#ifdef MF_TRACE
-            const long long _tc = clock64();
-#endif
+            const int q = tile * kTile + row;
+            const int qc = min(q, io.Q - 1);
+            QueryExt x = load_ext(ev.epi, io.ext, E, qc);
+            bool ok = mbar_wait(tfull + acc, ((uint32_t)i >> 1) & 1, err, 7, i);
             ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld below is warp-collective
             tc_fence_after();
             float l = __int_as_float(0x7fc00000);
             if (ok) {
                 TmemAcc tacc{tmem + (uint32_t)(acc * kAccCols) + ((uint32_t)(quad * 32) << 16),
-                             args.colscale ? args.colscale + ps.col0 : nullptr};
+                             ev.colscale ? ev.colscale + ps.col0 : nullptr};
                 bool bad = false;
-                l = pass_lnl<NM>(epi, ps, x, tacc, bad);
+                l = pass_lnl<NM>(ev.epi, ps, x, tacc, bad);
                 if (bad) l = __int_as_float(0x7fc00000);
             }
-            if (r == 0) TRACE_ADD(13, (unsigned long long)(clock64() - _tc));
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + acc);
-            if (q < args.Q) {
+            if (q < io.Q) {
                 if (np == 1) {
-                    args.out[q] = l;
-                    if (l != l) atomicAdd(epi.bad, 1ull);
+                    io.out[q] = l;
+                    if (l != l) atomicAdd(ev.epi.bad, 1ull);
                 } else {
-                    args.partial[(size_t)rank * args.Q + q] = l;
+                    io.partial[(size_t)rank * io.Q + q] = l;
                 }
             }
             if (!ok) break;
         }
-        if (r == 0) TRACE_SET(8, gtimer_ns());
     }
     __syncwarp();
     // no CTA may leave while a peer can still copy into it or signal it
     cluster_sync();
-    if (threadIdx.x == 0) TRACE_SET(9, gtimer_ns());
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
     }
+}
+
+template <int NM, int AT, int TERMS>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ TcCall call) {
+    SingleSrc src{&ev, &call};
+    tc_body<NM, AT, TERMS>(src, ev.epi.n_pass, call.nbox_max, call.sb, call.n_clusters, call.E, call.err);
+}
+
+template <int NM, int AT, int TERMS>
+__global__ void __launch_bounds__(kThreads, 1)
+tc_batch_kernel(const TcEvent *__restrict__ evs, const __grid_constant__ TcBatchCall call) {
+    BatchSrc src{evs, &call};
+    tc_body<NM, AT, TERMS>(src, call.np, call.nbox_max, call.sb, call.n_clusters, call.E, call.err);
 }
 
 // ----------------------------------------------------------- host side
@@ -756,64 +804,64 @@ int form_terms(mf_form f) {
     }
 }
 
+constexpr size_t kSmemMax = 227 * 1024;
+
+size_t smem_for(int terms, int np, int nbox_max, int sb) {
+    const int NA = (terms == 3) ? 2 : 1;
+    const int NB = (terms >= 2) ? 2 : 1;
+    return (size_t)1024 + (size_t)np * kSlotsPerProducer * NA * kATile + (size_t)sb * NB * nbox_max * kRowBytes +
+           (size_t)kProdWarps * 2 * kKB * sizeof(float4) + (2 * kMaxCluster * kSlotsPerProducer + 2 * kMaxStages + 5) * 8 +
+           16;
+}
+
+// The kernel a (form, mode count) pair runs, single-event or batched.
 template <int NM, int AT, int TERMS>
-int launch_nm(mf_handle *h, const TcArgs &a, cudaStream_t st) {
-    constexpr int NA = (TERMS == 3) ? 2 : 1;
-    constexpr int NB = (TERMS >= 2) ? 2 : 1;
-    const int np = (int)h->passes.size();
-    if (np > kMaxCluster) return MF_E_NOTIMPL;
-    TcArgs a2 = a;
-    a2.n_tiles = (a.Q + kTile - 1) / kTile;
-    auto smem_for = [&](int sb) {
-        return (size_t)1024 + (size_t)np * kSlotsPerProducer * NA * kATile +
-               (size_t)sb * NB * h->nbox * kRowBytes + (size_t)kProdWarps * 2 * kKB * sizeof(float4) +
-               (2 * kMaxCluster * kSlotsPerProducer + 2 * kMaxStages + 5) * 8 + 16;
-    };
-    a2.sb = h->tc_nbs ? h->tc_nbs : 4;
-    while (smem_for(a2.sb) > 227 * 1024 && a2.sb > 2) --a2.sb;
-    if (smem_for(a2.sb) > 227 * 1024) return MF_E_NOTIMPL;
-    // one CTA per SM (it owns all 512 TMEM columns): request > half the SM's shared memory
-    size_t bytes = std::max(smem_for(a2.sb), (size_t)120 * 1024);
-    auto kern = tc_kernel<NM, AT, TERMS>;
+void *pick3(bool batch) {
+    return batch ? (void *)tc_batch_kernel<NM, AT, TERMS> : (void *)tc_kernel<NM, AT, TERMS>;
+}
+template <int NM, int AT>
+void *pick2(int terms, bool batch) {
+    return terms == 1 ? pick3<NM, AT, 1>(batch) : terms == 2 ? pick3<NM, AT, 2>(batch) : pick3<NM, AT, 3>(batch);
+}
+template <int NM>
+void *pick1(int at, int terms, bool batch) {
+    return at == 0 ? pick2<NM, 0>(terms, batch) : pick2<NM, 1>(terms, batch);
+}
+void *pick_kernel(mf_form f, int n_modes, bool batch) {
+    const int at = form_type(f), terms = form_terms(f);
+    switch (n_modes) {
+        case 1: return pick1<1>(at, terms, batch);
+        case 2: return pick1<2>(at, terms, batch);
+        case 3: return pick1<3>(at, terms, batch);
+        case 4: return pick1<4>(at, terms, batch);
+        case 5: return pick1<5>(at, terms, batch);
+        default: return nullptr;
+    }
+}
+
+// Launch configuration shared by both kernels: cluster of np CTAs, one CTA
+// per SM (it owns all 512 TMEM columns: request > half the SM's shared
+// memory), as many clusters as can be resident at once.
+int tc_config(void *kern, int np, size_t smem, cudaStream_t st, cudaLaunchConfig_t &cfg,
+              cudaLaunchAttribute *attr, int *max_clusters) {
+    const size_t bytes = std::max(smem, (size_t)120 * 1024);
     MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
     if (np > 1) MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 0));
-    cudaLaunchConfig_t cfg = {};
+    cfg = cudaLaunchConfig_t{};
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = bytes;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)np;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // as many clusters as can be resident at once (each then loops over tiles)
-    int max_clusters = 0;
     cfg.gridDim = dim3((unsigned)np, 1, 1);
-    MF_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg));
-    if (max_clusters < 1) return MF_E_NOTIMPL;
-    a2.n_clusters = std::min(a2.n_tiles, max_clusters);
-    cfg.gridDim = dim3((unsigned)(a2.n_clusters * np), 1, 1);
-    CUtensorMap thi, tlo;
-    memcpy(&thi, h->tmap_hi, sizeof(thi));
-    memcpy(&tlo, h->tmap_lo, sizeof(tlo));
-    MF_CUDA(cudaLaunchKernelEx(&cfg, kern, thi, tlo, a2, make_rot(h), make_epi(h)));
+    *max_clusters = 0;
+    MF_CUDA(cudaOccupancyMaxActiveClusters(max_clusters, kern, &cfg));
+    if (*max_clusters < 1) return MF_E_NOTIMPL;
     return MF_OK;
-}
-
-template <int NM, int AT>
-int launch_terms(mf_handle *h, const TcArgs &a, cudaStream_t st) {
-    switch (form_terms(h->form)) {
-        case 1: return launch_nm<NM, AT, 1>(h, a, st);
-        case 2: return launch_nm<NM, AT, 2>(h, a, st);
-        default: return launch_nm<NM, AT, 3>(h, a, st);
-    }
-}
-
-template <int NM>
-int launch_type(mf_handle *h, const TcArgs &a, cudaStream_t st) {
-    return form_type(h->form) == 0 ? launch_terms<NM, 0>(h, a, st) : launch_terms<NM, 1>(h, a, st);
 }
 
 }  // namespace
@@ -852,41 +900,89 @@ int convert_tc_weights(mf_handle *h, mf_form f) {
     return make_tmap(h->tmap_lo, h->d_Wlo, at, h->Nk, h->Kdev, nbox);
 }
 
+int fill_tc_event(const mf_handle *h, TcEvent *ev) {
+    if (!h->d_Whi || !is_tc_form(h->form)) return MF_E_STATE;
+    memset(ev, 0, sizeof(*ev));
+    memcpy(&ev->tm_hi, h->tmap_hi, sizeof(CUtensorMap));
+    memcpy(&ev->tm_lo, h->tmap_lo, sizeof(CUtensorMap));
+    ev->epi = make_epi(h);
+    ev->rot = make_rot(h);
+    ev->nodes_s = h->d_nodes_s;
+    ev->colscale = form_type(h->form) == 0 ? h->d_colscale : nullptr;
+    ev->N = h->N;
+    ev->P = h->P;
+    ev->nkb = h->Nk / kKB;
+    ev->nbox = h->nbox;
+    return MF_OK;
+}
+
+size_t tc_smem_bytes(mf_form f, int np, int nbox_max, int sb) {
+    if (np < 1 || np > kMaxCluster || sb < 2 || sb > kMaxStages || nbox_max < 16 || nbox_max > kAccCols) return 0;
+    size_t b = smem_for(form_terms(f), np, nbox_max, sb);
+    return b <= kSmemMax ? b : 0;
+}
+
+int tc_batch_max_clusters(mf_form f, int n_modes, int np, int nbox_max, int sb, int *max_clusters) {
+    void *kern = pick_kernel(f, n_modes, true);
+    const size_t smem = tc_smem_bytes(f, np, nbox_max, sb);
+    if (!kern || !smem) return MF_E_NOTIMPL;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    return tc_config(kern, np, smem, nullptr, cfg, attr, max_clusters);
+}
+
+int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBatchCall &bc,
+                    cudaStream_t st) {
+    void *kern = pick_kernel(f, n_modes, true);
+    const size_t smem = tc_smem_bytes(f, bc.np, bc.nbox_max, bc.sb);
+    if (!kern || !smem) return MF_E_NOTIMPL;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    int maxc = 0;
+    int rc = tc_config(kern, bc.np, smem, st, cfg, attr, &maxc);
+    if (rc) return rc;
+    if (bc.n_clusters < 1 || bc.n_clusters > maxc) return MF_E_INVAL;
+    cfg.gridDim = dim3((unsigned)(bc.n_clusters * bc.np), 1, 1);
+    void *args[2] = {(void *)&d_events, (void *)&bc};
+    MF_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
+    return MF_OK;
+}
+
 int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
               cudaStream_t st, float *partial) {
     if (!h->d_Whi) return MF_E_STATE;
-    TcArgs a;
-    a.intr = intr;
-    a.ext = ext;
-    a.Q = Q;
-    a.E = E;
-    a.N = h->N;
-    a.P = h->P;
-    a.Nk = h->Nk;
-    a.nbox = h->nbox;
-    a.nodes_s = h->d_nodes_s;
-    a.colscale = form_type(h->form) == 0 ? h->d_colscale : nullptr;
-    a.out = out;
-    a.partial = partial;
-    a.phi_log2_scale = form_type(h->form) == 0 ? 14.f : 0.f;
-    switch (h->n_modes) {
-        case 1: return launch_type<1>(h, a, st);
-        case 2: return launch_type<2>(h, a, st);
-        case 3: return launch_type<3>(h, a, st);
-        case 4: return launch_type<4>(h, a, st);
-        case 5: return launch_type<5>(h, a, st);
-        default: return MF_E_NOTIMPL;
-    }
+    const int np = (int)h->passes.size();
+    if (np > kMaxCluster) return MF_E_NOTIMPL;
+    void *kern = pick_kernel(h->form, h->n_modes, false);
+    if (!kern) return MF_E_NOTIMPL;
+    TcEvent ev;
+    int rc = fill_tc_event(h, &ev);
+    if (rc) return rc;
+    TcCall c;
+    c.intr = intr;
+    c.ext = ext;
+    c.out = out;
+    c.partial = partial;
+    c.Q = Q;
+    c.E = E;
+    c.n_tiles = (Q + kTile - 1) / kTile;
+    c.nbox_max = h->nbox;
+    c.err = h->d_err;
+    c.sb = h->tc_nbs ? h->tc_nbs : 4;
+    while (!tc_smem_bytes(h->form, np, h->nbox, c.sb) && c.sb > 2) --c.sb;
+    const size_t smem = tc_smem_bytes(h->form, np, h->nbox, c.sb);
+    if (!smem) return MF_E_NOTIMPL;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    int maxc = 0;
+    rc = tc_config(kern, np, smem, st, cfg, attr, &maxc);
+    if (rc) return rc;
+    c.n_clusters = std::min(c.n_tiles, maxc);
+    cfg.gridDim = dim3((unsigned)(c.n_clusters * np), 1, 1);
+    void *args[2] = {(void *)&ev, (void *)&c};
+    MF_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
+    return MF_OK;
 }
 
 }  // namespace mf
 
-#ifdef MF_TRACE
-extern "C" __attribute__((visibility("default"))) int mf_debug_trace(unsigned long long *host, size_t n) {
-    if (n > 4096 * 16) n = 4096 * 16;
-    if (cudaMemcpyFromSymbol(host, mf::g_trace, n * 8) != cudaSuccess) return MF_E_CUDA;
-    static unsigned long long zero[4096 * 16];
-    if (cudaMemcpyToSymbol(mf::g_trace, zero, sizeof(zero)) != cudaSuccess) return MF_E_CUDA;
-    return MF_OK;
-}
-#endif
