@@ -269,6 +269,53 @@ MF_API int mf_loglike_batch(mf_handle *const *hs, int n_events, const float *con
                             const float *const *extrinsic, const int *Q, int E,
                             float *const *out_lnL, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Surrogate network (the learned part of the method's online stage): a
+ * fully connected network n_in -> hidden (x n_hidden) -> n_out with SiLU
+ * activations, FP32 master weights, BF16 GEMM operands and FP32
+ * accumulation, trained on the GPU by the library's own forward, backward
+ * and Adam kernels.  Layers l: z_l = W_l h_{l-1} + b_l, h_l = SiLU(z_l),
+ * output y = z_last; loss = mean over rows and outputs of (y - t)^2.
+ * Flat parameter order (set/get): per layer W_l [out][in] row-major, then
+ * b_l [out].
+ * Limits: 1 <= n_in <= 16; hidden a multiple of 16 up to 256; n_hidden >= 1
+ * (at most 7); n_out a multiple of 8.  MF_E_INVAL otherwise. */
+typedef struct mf_mlp mf_mlp;
+typedef struct mf_mlp_train_params {
+    int steps;                 /* Adam steps */
+    int batch;                 /* minibatch rows (multiple of 8; capped at n) */
+    float lr, lr_min;          /* cosine schedule from lr to lr_min over the steps */
+    float beta1, beta2, eps;   /* Adam constants; <= 0 selects 0.9, 0.999, 1e-8 */
+    unsigned long long seed;   /* minibatch order */
+} mf_mlp_train_params;
+/* Seeded initialisation: every W and b uniform in +-1/sqrt(fan_in). */
+MF_API int mf_mlp_create(int n_in, int hidden, int n_hidden, int n_out, unsigned long long seed,
+                         mf_mlp **out);
+MF_API void mf_mlp_free(mf_mlp *m);
+MF_API long long mf_mlp_n_params(const mf_mlp *m);
+/* Host FP32 arrays of mf_mlp_n_params floats; both synchronise the device. */
+MF_API int mf_mlp_set_params(mf_mlp *m, const float *host);
+MF_API int mf_mlp_get_params(const mf_mlp *m, float *host);
+/* Y [B][n_out] = network(X [B][n_in]); device FP32, Y 16-byte aligned.
+ * Asynchronous on `stream`. */
+MF_API int mf_mlp_forward(mf_mlp *m, const float *X, int B, float *Y, void *stream);
+/* Gradient of the loss on exactly the rows X [B][n_in], T [B][n_out]
+ * (device FP32, B a multiple of 8): host_grad (n_params floats, flat
+ * order) and *host_loss, either may be NULL.  Synchronous; parameters are
+ * unchanged.  MF_E_TIMEOUT if a bounded device wait gave up. */
+MF_API int mf_mlp_gradient(mf_mlp *m, const float *X, const float *T, int B, float *host_grad,
+                           double *host_loss, void *stream);
+/* Train on the n rows X [n][n_in], T [n][n_out] (device FP32): `steps`
+ * Adam steps on minibatches of `batch` rows taken in a scrambled order
+ * (row j of step s = (a_s + j c) mod n, a_s drawn from the seed and the
+ * step), one CUDA-graph replay per step.  Resets the Adam moments.
+ * Synchronous (waits for `stream`). */
+MF_API int mf_mlp_train(mf_mlp *m, const float *X, const float *T, int n,
+                        const mf_mlp_train_params *p, void *stream);
+/* "n_params", "loss" (mean squared residual of the last training step),
+ * "steps_done", "train_ms" (wall time of the last mf_mlp_train on the GPU). */
+MF_API int mf_mlp_query(const mf_mlp *m, const char *key, double *value);
+
 /* Tuning / instrumentation knobs (host-side, take effect at the next call):
  *   "timing"   : 1 = record CUDA events around the main lnL kernel of each
  *                mf_loglike (read back with mf_query "kernel_ms"), 0 = off.

@@ -14,7 +14,7 @@ import numpy as np
 
 from .build import SO as _SO_PATH, build
 
-__all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch",
+__all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch", "Mlp",
            "svd_compress", "FORMS", "pack_node_values"]
 
 MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
@@ -23,6 +23,13 @@ FORMS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16_wsplit": 3, "fp16_wsplit": 4,
          "bf16_3term": 5, "fp16_3term": 6}
 
 _lib = None
+
+
+class MlpTrainParams(ctypes.Structure):
+    """mf_mlp_train_params."""
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("lr", ctypes.c_float),
+                ("lr_min", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
 
 
 class MFError(RuntimeError):
@@ -69,6 +76,17 @@ def lib():
         L.mf_batch_free.argtypes = [vp]
         L.mf_batch_free.restype = None
         L.mf_loglike_batch.argtypes = [vp, ip, vp, vp, vp, ip, vp, vp]
+        L.mf_mlp_create.argtypes = [ip, ip, ip, ip, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+        L.mf_mlp_free.argtypes = [vp]
+        L.mf_mlp_free.restype = None
+        L.mf_mlp_n_params.argtypes = [vp]
+        L.mf_mlp_n_params.restype = ctypes.c_longlong
+        L.mf_mlp_set_params.argtypes = [vp, vp]
+        L.mf_mlp_get_params.argtypes = [vp, vp]
+        L.mf_mlp_forward.argtypes = [vp, vp, ip, vp, vp]
+        L.mf_mlp_gradient.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(dp), vp]
+        L.mf_mlp_train.argtypes = [vp, vp, vp, ip, ctypes.POINTER(MlpTrainParams), vp]
+        L.mf_mlp_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
         _lib = L
     return _lib
 
@@ -351,3 +369,74 @@ def loglike_batch(interpolants, intrinsic, extrinsic, out=None, stream=None):
     _check(lib().mf_loglike_batch(hs, len(interpolants), pi, pe, Q, E, po, _stream_ptr(stream)),
            "mf_loglike_batch")
     return out
+
+
+class Mlp:
+    """Owns an mf_mlp: the surrogate network (FP32 master weights, BF16 GEMMs
+    on tcgen05, FP32 accumulation) with GPU training."""
+
+    def __init__(self, n_in, hidden, n_hidden, n_out, seed=0):
+        m = ctypes.c_void_p()
+        _check(lib().mf_mlp_create(n_in, hidden, n_hidden, n_out, seed, ctypes.byref(m)),
+               "mf_mlp_create")
+        self._m = m
+        self.n_in, self.hidden, self.n_hidden, self.n_out = n_in, hidden, n_hidden, n_out
+
+    @property
+    def n_params(self):
+        return int(lib().mf_mlp_n_params(self._m))
+
+    def get_params(self):
+        buf = np.empty(self.n_params, np.float32)
+        _check(lib().mf_mlp_get_params(self._m, _ptr(buf)), "mf_mlp_get_params")
+        return buf
+
+    def set_params(self, flat):
+        buf = np.ascontiguousarray(flat, dtype=np.float32)
+        assert buf.size == self.n_params
+        _check(lib().mf_mlp_set_params(self._m, _ptr(buf)), "mf_mlp_set_params")
+
+    def forward(self, X, out=None, stream=None):
+        import torch
+        assert X.is_cuda and X.dtype == torch.float32 and X.is_contiguous()
+        B = X.shape[0]
+        if out is None:
+            out = torch.empty((B, self.n_out), dtype=torch.float32, device=X.device)
+        _check(lib().mf_mlp_forward(self._m, ctypes.c_void_p(X.data_ptr()), B,
+                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)),
+               "mf_mlp_forward")
+        return out
+
+    def gradient(self, X, T, stream=None):
+        """(flat gradient [n_params] float32, loss) on exactly these rows."""
+        g = np.empty(self.n_params, np.float32)
+        loss = ctypes.c_double()
+        _check(lib().mf_mlp_gradient(self._m, ctypes.c_void_p(X.data_ptr()),
+                                     ctypes.c_void_p(T.data_ptr()), X.shape[0], _ptr(g),
+                                     ctypes.byref(loss), _stream_ptr(stream)), "mf_mlp_gradient")
+        return g, loss.value
+
+    def train(self, X, T, steps, batch, lr, lr_min=None, seed=0, beta1=0.9, beta2=0.999,
+              eps=1e-8, stream=None):
+        p = MlpTrainParams(int(steps), int(batch), float(lr),
+                           float(lr if lr_min is None else lr_min), float(beta1), float(beta2),
+                           float(eps), int(seed))
+        _check(lib().mf_mlp_train(self._m, ctypes.c_void_p(X.data_ptr()),
+                                  ctypes.c_void_p(T.data_ptr()), X.shape[0], ctypes.byref(p),
+                                  _stream_ptr(stream)), "mf_mlp_train")
+
+    def query(self, key):
+        v = ctypes.c_double()
+        _check(lib().mf_mlp_query(self._m, key.encode(), ctypes.byref(v)), f"mf_mlp_query({key})")
+        return v.value
+
+    def close(self):
+        if getattr(self, "_m", None):
+            lib().mf_mlp_free(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

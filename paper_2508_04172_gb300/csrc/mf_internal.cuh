@@ -182,6 +182,8 @@ int tc_batch_max_clusters(mf_form f, int n_modes, int np, int nbox_max, int sb, 
 int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBatchCall &bc,
                     cudaStream_t st);
 bool is_tc_form(mf_form f);
+// tensor map of a 16-bit [rows][K] matrix (at: 0 = FP16, 1 = BF16), box K 32 x box_rows
+int make_tmap(void *out, void *base, int at, int K, int rows, int box_rows);
 }  // namespace mf
 
 #define MF_CUDA(call)                                                              \
