@@ -71,7 +71,8 @@ typedef enum {
     MF_FORM_BF16_WSPLIT = 3,
     MF_FORM_FP16_WSPLIT = 4,
     MF_FORM_BF16_3TERM = 5,
-    MF_FORM_FP16_3TERM = 6
+    MF_FORM_FP16_3TERM = 6,
+    MF_FORM_MLP = 7          /* trained surrogate network (mf_train_surrogate) */
 } mf_form;
 
 /* Name of a status code (static string). */
@@ -315,6 +316,41 @@ MF_API int mf_mlp_train(mf_mlp *m, const float *X, const float *T, int n,
 /* "n_params", "loss" (mean squared residual of the last training step),
  * "steps_done", "train_ms" (wall time of the last mf_mlp_train on the GPU). */
 MF_API int mf_mlp_query(const mf_mlp *m, const char *key, double *value);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate of a handle's interpolant (form MF_FORM_MLP).  A
+ * network 4 -> hidden (x n_hidden) -> K' (K' = K rounded up to 8), SiLU,
+ * maps the metric-eigenbasis point x = R (theta - centre) to the per-column
+ * standardised interpolated columns (node_values order); it is trained on
+ * the GPU (mf_mlp kernels) on n_train points labelled by the FP64 RBF
+ * interpolant, itself evaluated on the GPU (FP64 kernel sums and a cuBLAS
+ * DGEMM against the FP64 weights).
+ *   train_intrinsic : device [n_train][4] FP32 sampler-frame points (16-byte
+ *                     aligned), drawn from the region the sampler explores.
+ *   held_*          : device held-out queries [n_held][4], [n_held][E].
+ * The held-out gate compares the network's lnL with the plain FP32 RBF
+ * path's on the held-out queries: it passes when max |dlnL| <= gate_max and
+ * the median <= gate_median (defaults 0.1 and 0.01).  In MF_FORM_MLP,
+ * mf_loglike then evaluates the network (chunks of 65536 queries: input
+ * layer, hidden GEMMs, final GEMM fused with the lnL epilogue) and sends
+ * queries with |x| beyond the largest training |x| to the FP32 RBF path
+ * (the call synchronises its stream once to size that launch); if the gate
+ * failed, the RBF path serves every query.  mf_query: "fallback_rate",
+ * "surrogate_gate", "surrogate_heldout_max" / "_median" / "_p99",
+ * "surrogate_train_ms", "surrogate_label_ms", "surrogate_gate_ms",
+ * "surrogate_loss", "surrogate_r_gate", "surrogate_n_params".
+ * Synchronous; the handle keeps its form (select MF_FORM_MLP afterwards).
+ * Zero fields of the parameters select: steps 20000, batch 4096, hidden
+ * 256, n_hidden 3, lr 1e-3 -> lr_min 1e-5 (cosine). */
+typedef struct mf_surrogate_params {
+    int steps, batch, hidden, n_hidden;
+    float lr, lr_min;
+    float gate_max, gate_median;
+    unsigned long long seed;
+} mf_surrogate_params;
+MF_API int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train,
+                              const float *held_intrinsic, const float *held_extrinsic, int n_held,
+                              int E, const mf_surrogate_params *params, void *stream);
 
 /* Tuning / instrumentation knobs (host-side, take effect at the next call):
  *   "timing"   : 1 = record CUDA events around the main lnL kernel of each

@@ -20,9 +20,17 @@ __all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch", "
 MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
 MF_E_ILLCOND, MF_E_RANGE, MF_E_TIMEOUT, MF_E_NOTIMPL, MF_E_STATE = -4, -5, -6, -7, -8
 FORMS = {"fp32": 0, "bf16": 1, "fp16": 2, "bf16_wsplit": 3, "fp16_wsplit": 4,
-         "bf16_3term": 5, "fp16_3term": 6}
+         "bf16_3term": 5, "fp16_3term": 6, "mlp": 7}
 
 _lib = None
+
+
+class SurrogateParams(ctypes.Structure):
+    """mf_surrogate_params (zero fields select the library defaults)."""
+    _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("hidden", ctypes.c_int),
+                ("n_hidden", ctypes.c_int), ("lr", ctypes.c_float), ("lr_min", ctypes.c_float),
+                ("gate_max", ctypes.c_float), ("gate_median", ctypes.c_float),
+                ("seed", ctypes.c_ulonglong)]
 
 
 class MlpTrainParams(ctypes.Structure):
@@ -87,6 +95,8 @@ def lib():
         L.mf_mlp_gradient.argtypes = [vp, vp, vp, ip, vp, ctypes.POINTER(dp), vp]
         L.mf_mlp_train.argtypes = [vp, vp, vp, ip, ctypes.POINTER(MlpTrainParams), vp]
         L.mf_mlp_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
+        L.mf_train_surrogate.argtypes = [vp, vp, ip, vp, vp, ip, ip, ctypes.POINTER(SurrogateParams),
+                                         vp]
         _lib = L
     return _lib
 
@@ -241,6 +251,25 @@ class Interpolant:
 
     def set_option(self, key, value):
         _check(lib().mf_set_option(self._h, key.encode(), float(value)), f"mf_set_option({key})")
+
+    def train_surrogate(self, train_intrinsic, held_intrinsic, held_extrinsic, steps=0, batch=0,
+                        hidden=0, n_hidden=0, lr=0.0, lr_min=0.0, gate_max=0.0, gate_median=0.0,
+                        seed=0, stream=None):
+        """mf_train_surrogate with device tensors [n,4] (train) and [m,4], [m,E]
+        (held out); zero arguments take the library defaults.  Returns the
+        held-out statistics."""
+        p = SurrogateParams(int(steps), int(batch), int(hidden), int(n_hidden), float(lr),
+                            float(lr_min), float(gate_max), float(gate_median), int(seed))
+        P = ctypes.c_void_p
+        _check(lib().mf_train_surrogate(self._h, P(train_intrinsic.data_ptr()),
+                                        train_intrinsic.shape[0], P(held_intrinsic.data_ptr()),
+                                        P(held_extrinsic.data_ptr()), held_intrinsic.shape[0],
+                                        held_extrinsic.shape[1], ctypes.byref(p),
+                                        _stream_ptr(stream)), "mf_train_surrogate")
+        keys = ("surrogate_gate", "surrogate_heldout_max", "surrogate_heldout_median",
+                "surrogate_heldout_p99", "surrogate_train_ms", "surrogate_label_ms",
+                "surrogate_loss", "surrogate_r_gate")
+        return {k: self.query(k) for k in keys}
 
     def query(self, key):
         v = ctypes.c_double()

@@ -61,7 +61,7 @@ void free_form(mf_handle *h) {
 
 namespace mf {
 
-bool is_tc_form(mf_form f) { return f != MF_FORM_FP32; }
+bool is_tc_form(mf_form f) { return f >= MF_FORM_BF16 && f <= MF_FORM_FP16_3TERM; }
 
 // Split group widths w[0..n) into exactly `count` contiguous non-empty runs
 // minimising the widest run (each padded to kPassAlign); start[c] = first
@@ -214,6 +214,16 @@ RotParams make_rot(const mf_handle *h) {
 
 int prepare_form(mf_handle *h, mf_form f) {
     if (!h->have_layout) return MF_E_STATE;
+    if (f == MF_FORM_MLP) {
+        // the surrogate serves through the FP32 layout; its FP32 weights are the fallback
+        if (!h->sur) return MF_E_STATE;
+        int rc = prepare_form(h, MF_FORM_FP32);
+        if (rc) return rc;
+        rc = surrogate_prepare(h);
+        if (rc) return rc;
+        h->form = MF_FORM_MLP;
+        return MF_OK;
+    }
     free_form(h);
     h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : 176;
     h->pass_count = is_tc_form(f) ? h->pass_count_user : 0;   // exact counts: tcgen05 forms only
@@ -375,12 +385,13 @@ int mf_set_rotation(mf_handle *h, const double *metric, const double *centre) {
 }
 
 int mf_set_form(mf_handle *h, mf_form f) {
-    if (!h || f < MF_FORM_FP32 || f > MF_FORM_FP16_3TERM) return MF_E_INVAL;
+    if (!h || f < MF_FORM_FP32 || f > MF_FORM_MLP) return MF_E_INVAL;
+    if (f == MF_FORM_MLP && !h->sur) return MF_E_STATE;   // train the surrogate first
     if (!h->have_layout) {
         h->form = f;
         return MF_OK;
     }
-    if (f == h->form && (h->d_W32 || h->d_Whi)) return MF_OK;
+    if (f == h->form && f != MF_FORM_MLP && (h->d_W32 || h->d_Whi)) return MF_OK;
     return mf::prepare_form(h, f);
 }
 
@@ -404,6 +415,12 @@ int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int
     if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;   // rows are read as float4
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->form == MF_FORM_MLP) {
+        if (h->timing) MF_CUDA(cudaEventRecord(h->ev0, st));
+        int rc = mf::loglike_surrogate(h, intrinsic, extrinsic, Q, E, out_lnL, st, false);
+        if (h->timing) MF_CUDA(cudaEventRecord(h->ev1, st));
+        return rc;
+    }
     const int np = (int)h->passes.size();
     float *partial = nullptr;
     if (np > 1) {
@@ -507,6 +524,8 @@ int mf_query(const mf_handle *h, const char *key, double *value) {
     else if (k == "form") *value = (double)h->form;
     else if (k == "launches")
         *value = 1.0 + (h->passes.size() > 1 ? 1.0 : 0.0);
+    else if (k.compare(0, 9, "surrogate") == 0 || k == "fallback_rate")
+        return mf::surrogate_query(h, k, value);
     else if (k == "kernel_ms") {
         if (!h->timing) return MF_E_STATE;
         float ms = 0.f;
@@ -527,6 +546,7 @@ int mf_get_weights(const mf_handle *h, double *W_host, size_t count) {
 
 void mf_free(mf_handle *h) {
     if (!h) return;
+    mf::free_surrogate(h);
     free_form(h);
     if (h->d_nodes64) cudaFree(h->d_nodes64);
     if (h->d_W64) cudaFree(h->d_W64);

@@ -100,6 +100,8 @@ struct TcBatchCall {
 
 }  // namespace mf
 
+struct mf_surrogate;
+
 struct mf_handle {
     int dev = 0;
     int N = 0, K = 0, P = 0, tail_degree = 1;
@@ -155,6 +157,8 @@ struct mf_handle {
     unsigned int *d_err = nullptr;
     float *d_partial = nullptr;     // [n_pass][Q] partial lnL
     size_t partial_cap = 0;
+    // trained surrogate network (MF_FORM_MLP), or nullptr
+    mf_surrogate *sur = nullptr;
 };
 
 namespace mf {
@@ -182,6 +186,12 @@ int tc_batch_max_clusters(mf_form f, int n_modes, int np, int nbox_max, int sb, 
 int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBatchCall &bc,
                     cudaStream_t st);
 bool is_tc_form(mf_form f);
+// surrogate network (MF_FORM_MLP)
+int surrogate_prepare(mf_handle *h);
+void free_surrogate(mf_handle *h);
+int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+                      cudaStream_t st, bool force_net);
+int surrogate_query(const mf_handle *h, const std::string &key, double *value);
 // tensor map of a 16-bit [rows][K] matrix (at: 0 = FP16, 1 = BF16), box K 32 x box_rows
 int make_tmap(void *out, void *base, int at, int K, int rows, int box_rows);
 }  // namespace mf

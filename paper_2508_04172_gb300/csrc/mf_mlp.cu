@@ -526,3 +526,550 @@ int mf_mlp_query(const mf_mlp *m, const char *key, double *value) {
 }
 
 }  // extern "C"
+
+// ===================================================================
+// The surrogate of an interpolant handle: the network above trained to
+// map the metric-eigenbasis point x to the handle's interpolated columns
+// F(x) (Eq. rbfcoeff), labelled by the FP64 RBF interpolant on the GPU,
+// served through the same time-interpolation / amplitude / quadratic-form
+// epilogue as the RBF path (Eqs. SVD, projected_h_fd, logl_complete).
+// The plain FP32 RBF path is the fallback: for every query when the
+// held-out gate fails, and for queries outside the training radius.
+// ===================================================================
+
+#include <cublas_v2.h>
+
+struct mf_surrogate {
+    mf_mlp *net = nullptr;
+    int K = 0, K_out = 0;                 // user columns, network outputs (K rounded to 8)
+    double *d_mu = nullptr, *d_s = nullptr;   // per user column: mean, scale of the targets
+    float r_gate = 0.f;                   // largest |x| of the training set
+    bool gate = false;                    // held-out gate passed
+    double ho_max = 0, ho_median = 0, ho_p99 = 0;
+    float train_ms = 0, label_ms = 0, gate_ms = 0, loss = 0;
+    int n_train = 0;
+    // inference weights for the current device layout
+    __nv_bfloat16 *d_Wdev = nullptr;      // [Kdev][H] de-standardised final layer, device order
+    float *d_bdev = nullptr;              // [Kdev]
+    int Kdev = 0, nbox = 0;
+    unsigned layout_gen = ~0u;
+    // inference scratch (grown on demand)
+    int chunk_cap = 0;
+    __nv_bfloat16 *d_h[2] = {nullptr, nullptr};   // [chunk][H] ping-pong activations
+    float *d_part = nullptr;                      // [n_pass][chunk]
+    int q_cap = 0, e_cap = 0, np_cap = 0;
+    unsigned char *d_flag = nullptr;              // [Q] query outside the training radius
+    int *d_list = nullptr;                        // [Q] indices of those queries
+    int *d_count = nullptr;                       // number of them
+    float *d_ci = nullptr, *d_ce = nullptr, *d_co = nullptr, *d_cpart = nullptr;   // compacted copies
+    double fallback_rate = 0;
+};
+
+namespace mf {
+namespace {
+
+constexpr int kSurChunk = 1 << 16;       // queries per network chunk (activations stay in L2)
+constexpr int kLabelRows = 4096;         // label rows per FP64 GEMM
+
+// x = R (theta - centre) in FP64 and FP32; |x| per row.
+__global__ void sur_rotate_kernel(const float *__restrict__ th, int n, const double *__restrict__ Rc,
+                                  double *__restrict__ x64, float *__restrict__ x32, float *__restrict__ rad) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double d[4], r2 = 0.0;
+    for (int k = 0; k < 4; ++k) d[k] = (double)th[(size_t)i * 4 + k] - Rc[16 + k];
+    for (int a = 0; a < 4; ++a) {
+        double v = 0.0;
+        for (int k = 0; k < 4; ++k) v += Rc[4 * a + k] * d[k];
+        x64[(size_t)i * 4 + a] = v;
+        x32[(size_t)i * 4 + a] = (float)v;
+        r2 += v * v;
+    }
+    rad[i] = (float)sqrt(r2);
+}
+
+// Augmented RBF row of every point (Eq. rbfcoeff): exp(-eps^2 |x - y_n|^2)
+// for the N nodes, then the tail monomials 1, x_1..x_4 (first P of them).
+__global__ void sur_phi_kernel(const double *__restrict__ x, int rows, const double *__restrict__ nodes, int N,
+                               int P, double eps2, double *__restrict__ phi) {
+    const int NP = N + P;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)rows * NP;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / NP), n = (int)(idx % NP);
+        const double *xi = x + (size_t)i * 4;
+        double v;
+        if (n < N) {
+            const double *y = nodes + (size_t)n * 4;
+            double r2 = 0.0;
+            for (int k = 0; k < 4; ++k) r2 += (xi[k] - y[k]) * (xi[k] - y[k]);
+            v = exp(-eps2 * r2);
+        } else {
+            const int q = n - N;
+            v = q == 0 ? 1.0 : xi[q - 1];
+        }
+        phi[idx] = v;
+    }
+}
+
+// Per user column: mean and scale (standard deviation, floored at 1e-4 of
+// the largest column's) of the labels F [n][K].
+__global__ void sur_colstats_kernel(const double *__restrict__ F, int n, int K, double *__restrict__ mu,
+                                    double *__restrict__ sd) {
+    const int c = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v = F[(size_t)i * K + c];
+        s += v;
+        s2 += v * v;
+    }
+    __shared__ double a[256], b[256];
+    a[threadIdx.x] = s;
+    b[threadIdx.x] = s2;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) {
+            a[threadIdx.x] += a[threadIdx.x + k];
+            b[threadIdx.x] += b[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double m = a[0] / n;
+        mu[c] = m;
+        sd[c] = sqrt(fmax(0.0, b[0] / n - m * m));
+    }
+}
+
+__global__ void sur_floor_scale_kernel(double *sd, int K) {
+    double mx = 0.0;
+    for (int c = 0; c < K; ++c) mx = fmax(mx, sd[c]);
+    const double fl = fmax(1e-4 * mx, 1e-300);
+    for (int c = 0; c < K; ++c) sd[c] = fmax(sd[c], fl);
+}
+
+// Network targets (F - mu) / s in FP32 [n][K_out] (padding columns 0).
+__global__ void sur_targets_kernel(const double *__restrict__ F, int n, int K, int K_out,
+                                   const double *__restrict__ mu, const double *__restrict__ sd,
+                                   float *__restrict__ T) {
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)n * K_out;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / K_out), c = (int)(idx % K_out);
+        T[idx] = c < K ? (float)((F[(size_t)i * K + c] - mu[c]) / sd[c]) : 0.f;
+    }
+}
+
+// Final layer in the device column layout, de-standardised:
+// W_dev[d] = s_u W_L[u], b_dev[d] = s_u b_L[u] + mu_u (u = user column of d).
+__global__ void sur_devweights_kernel(const float *__restrict__ WL, const float *__restrict__ bL, int H,
+                                      const int *__restrict__ user_of_dev, int Kdev,
+                                      const double *__restrict__ mu, const double *__restrict__ sd,
+                                      __nv_bfloat16 *__restrict__ Wdev, float *__restrict__ bdev) {
+    const int d = blockIdx.x;
+    const int u = user_of_dev[d];
+    for (int k = threadIdx.x; k < H; k += blockDim.x)
+        Wdev[(size_t)d * H + k] = __float2bfloat16_rn(u >= 0 ? (float)(sd[u] * (double)WL[(size_t)u * H + k]) : 0.f);
+    if (threadIdx.x == 0) bdev[d] = u >= 0 ? (float)(sd[u] * (double)bL[u] + mu[u]) : 0.f;
+}
+
+// Network input layer for lnL queries: x = R (theta - centre) (FP32, as the
+// RBF path), first layer -> H1; flags queries with |x| > r_gate.
+__global__ void sur_input_kernel(const float *__restrict__ th, int Q, const RotParams rot,
+                                 const float *__restrict__ W1, const float *__restrict__ b1, int H,
+                                 __nv_bfloat16 *__restrict__ H1, float r_gate, unsigned char *__restrict__ flag,
+                                 int *__restrict__ count) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)Q * H) return;
+    const int q = (int)(idx / H), o = (int)(idx % H);
+    const float4 t = *reinterpret_cast<const float4 *>(th + (size_t)q * 4);
+    const float d[4] = {t.x - rot.centre[0], t.y - rot.centre[1], t.z - rot.centre[2], t.w - rot.centre[3]};
+    float x[4], r2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        x[a] = rot.R[4 * a] * d[0] + rot.R[4 * a + 1] * d[1] + rot.R[4 * a + 2] * d[2] + rot.R[4 * a + 3] * d[3];
+        r2 = fmaf(x[a], x[a], r2);
+    }
+    float z = b1[o];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) z = fmaf(W1[o * 4 + a], x[a], z);
+    H1[idx] = __float2bfloat16_rn(silu_f(z));
+    if (o == 0 && flag) {
+        const bool out = !(sqrtf(r2) <= r_gate);
+        flag[q] = out;
+        if (out) atomicAdd(count, 1);
+    }
+}
+
+// Gather the flagged queries (any order) into compact copies.
+__global__ void sur_compact_kernel(const unsigned char *__restrict__ flag, int Q, const float *__restrict__ th,
+                                   const float *__restrict__ ext, int E, int *__restrict__ slot,
+                                   int *__restrict__ list, float *__restrict__ ci, float *__restrict__ ce) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q || !flag[q]) return;
+    const int j = atomicAdd(slot, 1);
+    list[j] = q;
+    reinterpret_cast<float4 *>(ci)[j] = reinterpret_cast<const float4 *>(th)[q];
+    for (int k = 0; k < E; ++k) ce[(size_t)j * E + k] = ext[(size_t)q * E + k];
+}
+
+__global__ void sur_scatter_kernel(const int *__restrict__ list, const int *__restrict__ count,
+                                   const float *__restrict__ v, float *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < *count) out[list[j]] = v[j];
+}
+
+void free_infer(mf_surrogate *s) {
+    auto fr = [](void *p) { if (p) cudaFree(p); };
+    fr(s->d_h[0]); fr(s->d_h[1]); fr(s->d_part);
+    fr(s->d_flag); fr(s->d_list); fr(s->d_count); fr(s->d_ci); fr(s->d_ce); fr(s->d_co); fr(s->d_cpart);
+    s->d_h[0] = s->d_h[1] = nullptr;
+    s->d_part = nullptr;
+    s->d_flag = nullptr;
+    s->d_list = s->d_count = nullptr;
+    s->d_ci = s->d_ce = s->d_co = s->d_cpart = nullptr;
+    s->chunk_cap = s->q_cap = s->e_cap = s->np_cap = 0;
+}
+
+void destroy_surrogate(mf_surrogate *s) {
+    if (!s) return;
+    free_infer(s);
+    if (s->net) destroy_mlp(s->net);
+    auto fr = [](void *p) { if (p) cudaFree(p); };
+    fr(s->d_mu); fr(s->d_s); fr(s->d_Wdev); fr(s->d_bdev);
+    delete s;
+}
+
+int ensure_infer(mf_surrogate *s, int chunk, int Q, int E, int n_pass) {
+    const int H = s->net->H;
+    if (chunk > s->chunk_cap) {
+        for (int k = 0; k < 2; ++k) {
+            if (s->d_h[k]) cudaFree(s->d_h[k]);
+            s->d_h[k] = nullptr;
+        }
+        if (s->d_part) cudaFree(s->d_part);
+        s->d_part = nullptr;
+        s->chunk_cap = 0;
+        MF_CUDA(cudaMalloc((void **)&s->d_h[0], 2 * (size_t)chunk * H));
+        MF_CUDA(cudaMalloc((void **)&s->d_h[1], 2 * (size_t)chunk * H));
+        MF_CUDA(cudaMalloc((void **)&s->d_part, 4 * (size_t)chunk * kMaxPass));
+        s->chunk_cap = chunk;
+    }
+    if (Q > s->q_cap || E > s->e_cap || n_pass > s->np_cap) {
+        auto fr = [](void *p) { if (p) cudaFree(p); };
+        fr(s->d_flag); fr(s->d_list); fr(s->d_count); fr(s->d_ci); fr(s->d_ce); fr(s->d_co); fr(s->d_cpart);
+        s->q_cap = s->e_cap = s->np_cap = 0;
+        const size_t q = (size_t)Q, e = (size_t)std::max(E, 5);
+        MF_CUDA(cudaMalloc((void **)&s->d_flag, q));
+        MF_CUDA(cudaMalloc((void **)&s->d_list, 4 * q));
+        MF_CUDA(cudaMalloc((void **)&s->d_count, 8));
+        MF_CUDA(cudaMalloc((void **)&s->d_ci, 16 * q));
+        MF_CUDA(cudaMalloc((void **)&s->d_ce, 4 * q * e));
+        MF_CUDA(cudaMalloc((void **)&s->d_co, 4 * q));
+        MF_CUDA(cudaMalloc((void **)&s->d_cpart, 4 * q * (size_t)n_pass));
+        s->q_cap = (int)q;
+        s->e_cap = (int)e;
+        s->np_cap = n_pass;
+    }
+    return MF_OK;
+}
+
+}  // namespace
+
+// Final-layer weights of the surrogate in the handle's current device
+// layout (rebuilt whenever the layout changes).
+int surrogate_prepare(mf_handle *h) {
+    mf_surrogate *s = h->sur;
+    if (!s || !s->net) return MF_E_STATE;
+    const int H = s->net->H, L = s->net->L;
+    if (s->d_Wdev) cudaFree(s->d_Wdev);
+    if (s->d_bdev) cudaFree(s->d_bdev);
+    s->d_Wdev = nullptr;
+    s->d_bdev = nullptr;
+    MF_CUDA(cudaMalloc((void **)&s->d_Wdev, 2 * (size_t)h->Kdev * H));
+    MF_CUDA(cudaMalloc((void **)&s->d_bdev, 4 * (size_t)h->Kdev));
+    const float *WL = s->net->d_p + s->net->off[L - 1];
+    sur_devweights_kernel<<<h->Kdev, 256>>>(WL, WL + (size_t)s->K_out * H, H, h->d_user_of_dev, h->Kdev, s->d_mu,
+                                            s->d_s, s->d_Wdev, s->d_bdev);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaDeviceSynchronize());
+    s->Kdev = h->Kdev;
+    int nbox = 0;
+    for (auto &p : h->passes) nbox = std::max(nbox, p.width);
+    s->nbox = nbox;
+    return MF_OK;
+}
+
+void free_surrogate(mf_handle *h) {
+    destroy_surrogate(h->sur);
+    h->sur = nullptr;
+}
+
+// lnL through the network: chunks of queries through the hidden layers,
+// the final layer fused with the lnL epilogue per column pass, then the
+// plain FP32 RBF path for queries outside the training radius.  Uses the
+// FP32 weights of the handle (prepared with the surrogate form).
+int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+                      cudaStream_t st, bool force_net) {
+    mf_surrogate *s = h->sur;
+    if (!s || !s->net || !s->d_Wdev || !h->d_W32) return MF_E_STATE;
+    const int np = (int)h->passes.size();
+    if (!s->gate && !force_net) {   // held-out gate failed: the RBF path serves everything
+        s->fallback_rate = 1.0;
+        int rc = ensure_infer(s, 1, Q, E, np);
+        if (rc) return rc;
+        rc = launch_fp32(h, intr, ext, Q, E, out, st, np > 1 ? s->d_cpart : nullptr);
+        if (rc) return rc;
+        if (np > 1) return launch_combine(s->d_cpart, np, Q, out, st, h->d_bad);
+        return MF_OK;
+    }
+    mf_mlp *m = s->net;
+    const int H = m->H;
+    const int chunk = std::min(Q, kSurChunk);
+    int rc = ensure_infer(s, chunk, Q, E, np);
+    if (rc) return rc;
+    MF_CUDA(cudaMemsetAsync(s->d_count, 0, 8, st));
+    const RotParams rot = make_rot(h);
+    const EpiParams epi = make_epi(h);
+    for (int q0 = 0; q0 < Q; q0 += chunk) {
+        const int Qc = std::min(chunk, Q - q0);
+        const long long n1 = (long long)Qc * H;
+        sur_input_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(
+            intr + (size_t)q0 * 4, Qc, rot, m->d_p, m->d_p + H * 4, H, s->d_h[0], force_net ? 1e30f : s->r_gate,
+            s->d_flag + q0, s->d_count);
+        MF_CUDA(cudaGetLastError());
+        int cur = 0;
+        for (int l = 1; l < m->L - 1; ++l) {
+            GemmArgs g{};
+            g.bias = m->d_p + m->off[l] + H * H;
+            g.out_bf = s->d_h[cur ^ 1];
+            GemmPlan pl;
+            rc = make_plan(pl, EPI_SILU, s->d_h[cur], Qc, H, m->W[l], H, nt_for(H), g, h->d_err);
+            if (rc) return rc;
+            rc = launch_plan(pl, st);
+            if (rc) return rc;
+            cur ^= 1;
+        }
+        GemmArgs g{};
+        g.bias = s->d_bdev;
+        g.ext = ext + (size_t)q0 * E;
+        g.E = E;
+        g.lnl_out = out + q0;
+        g.partial = s->d_part;
+        GemmPlan pl;
+        rc = make_plan(pl, EPI_LNL, s->d_h[cur], Qc, H, s->d_Wdev, h->Kdev, s->nbox, g, h->d_err);
+        if (rc) return rc;
+        pl.grid_y = np;
+        rc = launch_plan(pl, st, &epi, h->n_modes);
+        if (rc) return rc;
+        if (np > 1) {
+            rc = launch_combine(s->d_part, np, Qc, out + q0, st, h->d_bad);
+            if (rc) return rc;
+        }
+    }
+    if (force_net) {
+        s->fallback_rate = 0.0;
+        return MF_OK;
+    }
+    // queries outside the training radius: plain RBF (the count sizes that launch)
+    int nfb = 0;
+    MF_CUDA(cudaMemcpyAsync(&nfb, s->d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    s->fallback_rate = (double)nfb / (double)Q;
+    if (nfb == 0) return MF_OK;
+    MF_CUDA(cudaMemsetAsync(s->d_count + 1, 0, 4, st));
+    sur_compact_kernel<<<(Q + 255) / 256, 256, 0, st>>>(s->d_flag, Q, intr, ext, E, s->d_count + 1, s->d_list,
+                                                        s->d_ci, s->d_ce);
+    MF_CUDA(cudaGetLastError());
+    rc = launch_fp32(h, s->d_ci, s->d_ce, nfb, E, s->d_co, st, np > 1 ? s->d_cpart : nullptr);
+    if (rc) return rc;
+    if (np > 1) {
+        rc = launch_combine(s->d_cpart, np, nfb, s->d_co, st, h->d_bad);
+        if (rc) return rc;
+    }
+    sur_scatter_kernel<<<(nfb + 255) / 256, 256, 0, st>>>(s->d_list, s->d_count, s->d_co, out);
+    MF_CUDA(cudaGetLastError());
+    return MF_OK;
+}
+
+}  // namespace mf
+
+namespace {
+
+// host-side quantiles of |a - b| over finite pairs
+void abs_diff_stats(const std::vector<float> &a, const std::vector<float> &b, double &mx, double &med, double &p99) {
+    std::vector<double> d;
+    d.reserve(a.size());
+    for (size_t i = 0; i < a.size(); ++i)
+        if (std::isfinite(a[i]) && std::isfinite(b[i])) d.push_back(std::fabs((double)a[i] - (double)b[i]));
+    mx = med = p99 = d.empty() ? INFINITY : 0.0;
+    if (d.empty()) return;
+    std::sort(d.begin(), d.end());
+    mx = d.back();
+    med = d[d.size() / 2];
+    p99 = d[std::min(d.size() - 1, (size_t)(0.99 * (double)d.size()))];
+}
+
+}  // namespace
+
+extern "C" {
+
+int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train, const float *held_intrinsic,
+                       const float *held_extrinsic, int n_held, int E, const mf_surrogate_params *sp,
+                       void *stream) {
+    if (!h || !train_intrinsic || !sp || n_train < 64 || E < 5) return MF_E_INVAL;
+    if (n_held < 0 || (n_held > 0 && (!held_intrinsic || !held_extrinsic))) return MF_E_INVAL;
+    if (((uintptr_t)train_intrinsic & 15) || ((uintptr_t)held_intrinsic & 15)) return MF_E_INVAL;
+    if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    MF_CUDA(cudaStreamSynchronize(st));
+    const mf_form prev = h->form;
+    mf::free_surrogate(h);
+    mf_surrogate *s = new (std::nothrow) mf_surrogate();
+    if (!s) return MF_E_NOMEM;
+    h->sur = s;
+    s->K = h->K;
+    s->K_out = (h->K + 7) / 8 * 8;
+    s->n_train = n_train;
+    const int hidden = sp->hidden > 0 ? sp->hidden : 256;
+    const int n_hidden = sp->n_hidden > 0 ? sp->n_hidden : 3;
+    int rc = mf_mlp_create(4, hidden, n_hidden, s->K_out, sp->seed, &s->net);
+    if (rc) { mf::free_surrogate(h); return rc; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    // ---- labels: the FP64 RBF interpolant at the rotated training points
+    cudaEventRecord(e0, st);
+    const int NP = h->N + h->P, K = h->K;
+    double *x64 = nullptr, *Rc = nullptr, *F = nullptr, *phi = nullptr;
+    float *x32 = nullptr, *rad = nullptr, *T = nullptr;
+    auto cleanup = [&]() {
+        for (void *p : {(void *)x64, (void *)Rc, (void *)F, (void *)phi, (void *)x32, (void *)rad, (void *)T})
+            if (p) cudaFree(p);
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    };
+    const int lrows = std::min(n_train, mf::kLabelRows);
+    bool ok = cudaMalloc((void **)&x64, 32 * (size_t)n_train) == cudaSuccess &&
+              cudaMalloc((void **)&Rc, 20 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc((void **)&F, 8 * (size_t)n_train * K) == cudaSuccess &&
+              cudaMalloc((void **)&phi, 8 * (size_t)lrows * NP) == cudaSuccess &&
+              cudaMalloc((void **)&x32, 16 * (size_t)n_train) == cudaSuccess &&
+              cudaMalloc((void **)&rad, 4 * (size_t)n_train) == cudaSuccess &&
+              cudaMalloc((void **)&T, 4 * (size_t)n_train * s->K_out) == cudaSuccess &&
+              cudaMalloc((void **)&s->d_mu, 8 * (size_t)K) == cudaSuccess &&
+              cudaMalloc((void **)&s->d_s, 8 * (size_t)K) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        cleanup();
+        mf::free_surrogate(h);
+        return MF_E_NOMEM;
+    }
+    double Rh[20];
+    memcpy(Rh, h->R, 16 * sizeof(double));
+    memcpy(Rh + 16, h->centre, 4 * sizeof(double));
+    cudaMemcpy(Rc, Rh, sizeof(Rh), cudaMemcpyHostToDevice);
+    mf::sur_rotate_kernel<<<(n_train + 255) / 256, 256, 0, st>>>(train_intrinsic, n_train, Rc, x64, x32, rad);
+    cublasHandle_t cb = nullptr;
+    if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) { cleanup(); mf::free_surrogate(h); return MF_E_CUDA; }
+    cublasSetStream(cb, st);
+    const double one = 1.0, zero = 0.0;
+    for (int r0 = 0; r0 < n_train && rc == MF_OK; r0 += lrows) {
+        const int rows = std::min(lrows, n_train - r0);
+        mf::sur_phi_kernel<<<1024, 256, 0, st>>>(x64 + (size_t)r0 * 4, rows, h->d_nodes64, h->N, h->P,
+                                                 h->eps * h->eps, phi);
+        // row-major F[rows][K] = Phi[rows][NP] W[NP][K]  (column-major: F^T = W^T Phi^T)
+        if (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, K, rows, NP, &one, h->d_W64, K, phi, NP, &zero,
+                        F + (size_t)r0 * K, K) != CUBLAS_STATUS_SUCCESS)
+            rc = MF_E_CUDA;
+    }
+    cublasDestroy(cb);
+    if (rc) { cleanup(); mf::free_surrogate(h); return rc; }
+    mf::sur_colstats_kernel<<<K, 256, 0, st>>>(F, n_train, K, s->d_mu, s->d_s);
+    mf::sur_floor_scale_kernel<<<1, 1, 0, st>>>(s->d_s, K);
+    mf::sur_targets_kernel<<<1024, 256, 0, st>>>(F, n_train, K, s->K_out, s->d_mu, s->d_s, T);
+    cudaEventRecord(e1, st);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    if (ce != cudaSuccess) { cleanup(); mf::free_surrogate(h); MF_CUDA(ce); }
+    cudaEventElapsedTime(&s->label_ms, e0, e1);
+    {
+        std::vector<float> r(n_train);
+        cudaMemcpy(r.data(), rad, 4 * (size_t)n_train, cudaMemcpyDeviceToHost);
+        s->r_gate = *std::max_element(r.begin(), r.end());
+    }
+    // ---- training
+    mf_mlp_train_params tp{};
+    tp.steps = sp->steps > 0 ? sp->steps : 20000;
+    tp.batch = sp->batch > 0 ? sp->batch : 4096;
+    tp.lr = sp->lr > 0 ? sp->lr : 1e-3f;
+    tp.lr_min = sp->lr_min > 0 ? sp->lr_min : 1e-5f;
+    tp.seed = sp->seed;
+    rc = mf_mlp_train(s->net, x32, T, n_train, &tp, stream);
+    s->train_ms = s->net->train_ms;
+    double loss = 0;
+    if (rc == MF_OK) rc = mf_mlp_query(s->net, "loss", &loss);
+    s->loss = (float)loss;
+    cleanup();
+    if (rc) { mf::free_surrogate(h); return rc; }
+    // ---- held-out gate: the network's lnL against the plain FP32 RBF path
+    rc = mf::prepare_form(h, MF_FORM_FP32);
+    if (rc == MF_OK) rc = mf::surrogate_prepare(h);
+    if (rc == MF_OK && n_held > 0) {
+        float *a = nullptr, *b = nullptr;
+        if (cudaMalloc((void **)&a, 4 * (size_t)n_held) != cudaSuccess ||
+            cudaMalloc((void **)&b, 4 * (size_t)n_held) != cudaSuccess) {
+            cudaGetLastError();
+            rc = MF_E_NOMEM;
+        } else {
+            cudaEvent_t g0, g1;
+            cudaEventCreate(&g0);
+            cudaEventCreate(&g1);
+            cudaEventRecord(g0, st);
+            rc = mf::loglike_surrogate(h, held_intrinsic, held_extrinsic, n_held, E, a, st, true);
+            cudaEventRecord(g1, st);
+            if (rc == MF_OK) rc = mf_loglike(h, held_intrinsic, held_extrinsic, n_held, E, b, stream);
+            if (rc == MF_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = MF_E_CUDA;
+            cudaEventElapsedTime(&s->gate_ms, g0, g1);
+            cudaEventDestroy(g0);
+            cudaEventDestroy(g1);
+            if (rc == MF_OK) {
+                std::vector<float> ha(n_held), hb(n_held);
+                cudaMemcpy(ha.data(), a, 4 * (size_t)n_held, cudaMemcpyDeviceToHost);
+                cudaMemcpy(hb.data(), b, 4 * (size_t)n_held, cudaMemcpyDeviceToHost);
+                abs_diff_stats(ha, hb, s->ho_max, s->ho_median, s->ho_p99);
+            }
+        }
+        if (a) cudaFree(a);
+        if (b) cudaFree(b);
+        // the held-out runs' out-of-window counts are not the caller's
+        long long nb = 0;
+        if (mf_sync_status(h, stream, &nb) == MF_E_TIMEOUT && rc == MF_OK) rc = MF_E_TIMEOUT;
+    }
+    const float gmax = sp->gate_max > 0 ? sp->gate_max : 0.1f;
+    const float gmed = sp->gate_median > 0 ? sp->gate_median : 0.01f;
+    s->gate = rc == MF_OK && n_held > 0 && s->ho_max <= gmax && s->ho_median <= gmed;
+    // back to the caller's form (the surrogate stays trained)
+    int rc2 = mf::prepare_form(h, prev);
+    if (rc) { mf::free_surrogate(h); return rc; }
+    return rc2;
+}
+
+}  // extern "C"
+
+namespace mf {
+int surrogate_query(const mf_handle *h, const std::string &k, double *v) {
+    const mf_surrogate *s = h->sur;
+    if (!s) return MF_E_STATE;
+    if (k == "fallback_rate") *v = s->fallback_rate;
+    else if (k == "surrogate_gate") *v = s->gate ? 1.0 : 0.0;
+    else if (k == "surrogate_heldout_max") *v = s->ho_max;
+    else if (k == "surrogate_heldout_median") *v = s->ho_median;
+    else if (k == "surrogate_heldout_p99") *v = s->ho_p99;
+    else if (k == "surrogate_train_ms") *v = s->train_ms;
+    else if (k == "surrogate_label_ms") *v = s->label_ms;
+    else if (k == "surrogate_gate_ms") *v = s->gate_ms;
+    else if (k == "surrogate_loss") *v = s->loss;
+    else if (k == "surrogate_r_gate") *v = s->r_gate;
+    else if (k == "surrogate_n_params") *v = (double)s->net->n_params;
+    else return MF_E_INVAL;
+    return MF_OK;
+}
+}  // namespace mf
