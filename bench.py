@@ -11,6 +11,8 @@ FP32 form, the kernel's roofline fraction, an end-to-end number through the C
 ABI with host buffers, and the FP64 CPU oracle timed on this host.
 
   python bench.py [--gpus N --steps K --warmup W --config C1 --forms fp32,fp16_3term]
+  python bench.py --config C4 --forms fp32,fp16_3term,mlp   # + learned surrogate
+  python bench.py --config C3        # 100 events, one persistent launch + CUDA graph
   python bench.py --impl reference ...   # FP64 CPU oracle arm
 """
 from __future__ import annotations
@@ -224,6 +226,14 @@ def run_ours(args):
     ref = om.loglike(th[sample], ex[sample])
     forms = [f.strip() for f in args.forms.split(",") if f.strip()]
     res = {}
+    sur = None
+    if "mlp" in forms:
+        # surrogate: 10^5 training points and 10^4 held-out queries drawn like the batch
+        from workload.standin import make_queries
+        tth, _ = make_queries(ev, 100000, seed=spec.seed + 101)
+        hth, hex_ = make_queries(ev, 10000, seed=spec.seed + 102)
+        sur = m.train_surrogate(torch.from_numpy(tth).to(dev), torch.from_numpy(hth).to(dev),
+                                torch.from_numpy(hex_).to(dev), seed=1)
     for f in forms:
         try:
             m.set_form(f)
@@ -236,6 +246,8 @@ def run_ours(args):
         err = np.abs(got - ref)
         res[f] = {"max_abs_dlnl": float(err.max()), "p99_abs_dlnl": float(np.quantile(err, 0.99)),
                   "median_abs_dlnl": float(np.median(err)), "n_checked": int(len(sample))}
+        if f == "mlp":
+            res[f]["fallback_rate"] = m.query("fallback_rate")
     # timing
     clocks = Clocks(local)
     if world > 1:
@@ -254,7 +266,7 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ck = clocks.summary()
-    ok = [f for f in forms if "error" not in res[f] and res[f]["max_abs_dlnl"] <= TOL]
+    ok = [f for f in forms if "error" not in res[f] and res[f]["max_abs_dlnl"] <= TOL and f != "mlp"]
     plain = "fp32"
     chosen = min(ok, key=lambda f: res[f]["ms_per_step"]) if ok else plain
     ms = res[chosen]["ms_per_step"]
@@ -320,6 +332,30 @@ def run_ours(args):
                       for f, r in res.items() if "error" not in r},
             "speedup_vs_plain_fp32": (round(res[plain]["ms_per_step"] / ms, 3)
                                       if plain in res and "error" not in res[plain] else None)}
+    if sur is not None and "mlp" in res and "error" not in res["mlp"]:
+        r = res["mlp"]
+        H = 256
+        Ko = (K + 7) // 8 * 8
+        fl = 2.0 * (4 * H + 2 * H * H + H * Ko)
+        line["surrogate"] = {
+            "network": f"4->{H}->{H}->{H}->{Ko}, SiLU, BF16 GEMMs (tcgen05), FP32 accumulation",
+            "gate_passed": bool(sur["surrogate_gate"]),
+            "heldout_vs_fp32_rbf": {"max": sur["surrogate_heldout_max"],
+                                    "median": sur["surrogate_heldout_median"],
+                                    "p99": sur["surrogate_heldout_p99"], "n": 10000},
+            "vs_fp64_oracle": {k: r[k] for k in ("max_abs_dlnl", "p99_abs_dlnl", "median_abs_dlnl",
+                                                 "n_checked")},
+            "evals_per_s": round(Q * world / (r["ms_per_step"] / 1e3), 1),
+            "ms_per_step": round(r["ms_per_step"], 4),
+            "speedup_vs_plain_fp32": (round(res[plain]["ms_per_step"] / r["ms_per_step"], 2)
+                                      if plain in res and "error" not in res[plain] else None),
+            "speedup_vs_chosen_form": round(ms / r["ms_per_step"], 2),
+            "fallback_rate": r.get("fallback_rate"),
+            "train_ms": round(sur["surrogate_train_ms"], 1),
+            "label_ms": round(sur["surrogate_label_ms"], 1),
+            "final_train_loss": sur["surrogate_loss"],
+            "tensor_tflops": round(fl * Q / (r["kernel_ms"] / 1e3) / 1e12, 2),
+            "flops_per_eval": fl}
     # CPU FP64 oracle on this host (rank 0, N = 1 only)
     if rank == 0 and world == 1:
         _, _, n, rate, cores = oracle_baseline(ev, th, ex, budget_s=args.cpu_budget)
@@ -333,13 +369,204 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """C3: 100 events with uneven N, rank and Q in one persistent tcgen05 launch
+    replayed from a CUDA graph (launch shape chosen by the library's autotuner),
+    against the same events as separate mf_loglike calls and the plain FP32
+    form."""
+    import torch
+    import paper_2508_04172_gb300 as mf
+    from workload import standin
+    from workload.standin import c3_specs, make_event, make_queries
+    import oracle  # noqa: F401  (test infrastructure: accuracy + CPU baseline only)
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    form = "fp16_3term"
+    specs = c3_specs()
+    t0 = time.perf_counter()
+    evs, models, th, ex = [], [], [], []
+    for sp in specs:
+        ev = make_event(sp)
+        models.append(mf.Interpolant.from_overlaps(
+            ev.nodes, standin.node_overlaps(ev), standin.standin_sigma(ev, ev.nodes), sp.rank,
+            sp.eps, sp.modes, ev.det, sp.t0, sp.dt, sp.d_ref, ev.metric, ev.centre, sp.tail_degree,
+            form))
+        a, b = make_queries(ev, sp.Q, seed=sp.seed + 17 + 1000 * rank)
+        evs.append(ev)
+        th.append(a)
+        ex.append(b)
+    build_s = time.perf_counter() - t0
+    Qs = [sp.Q for sp in specs]
+    Qtot = sum(Qs)
+    t1 = time.perf_counter()
+    bt = mf.Batch(models, Qs, autotune=True)
+    tune_s = time.perf_counter() - t1
+    table = [[a, r, round(t, 3)] for a, r, t in bt.tuning()]
+    shape = (int(bt.query("n_pass")), int(bt.query("ring")), int(bt.query("clusters")))
+    d_th = [torch.from_numpy(a).to(dev) for a in th]
+    d_ex = [torch.from_numpy(b).to(dev) for b in ex]
+    outs = [torch.empty(q, dtype=torch.float32, device=dev) for q in Qs]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    st = torch.cuda.current_stream()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()                   # evict L2 (256 MB > 129 MB L2), not timed
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            fn()
+            e1.record(st)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts
+
+    def batch_step():
+        bt.loglike(d_th, d_ex, outs)
+
+    clocks = Clocks(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    bt.set_option("timing", 1)
+    ts, kern = [], []
+    with clocks:
+        torch.cuda.nvtx.range_push("timed_batch")
+        for _ in range(args.warmup):
+            batch_step()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            ts += timed(batch_step, 1, 0)
+            kern.append(bt.query("kernel_ms"))
+        torch.cuda.nvtx.range_pop()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ck = clocks.summary()
+    bt.set_option("timing", 0)
+    ms = statistics.mean(ts)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    status = bt.sync_status()[0]
+    got = [o.cpu().numpy() for o in outs]
+
+    # the same events as separate calls (same form and layout), then the plain FP32 form
+    def loop():
+        for mm, a, b, o in zip(models, d_th, d_ex, outs):
+            mm.loglike(a, b, out=o)
+    loop_ms = statistics.mean(timed(loop, max(3, args.steps // 4), 2))
+    same = all(np.array_equal(g, o.cpu().numpy()) for g, o in zip(got, outs))
+    rates = []
+    for mm, a, b, o, q in zip(models, d_th, d_ex, outs, Qs):
+        r = statistics.median(timed(lambda: mm.loglike(a, b, out=o), 3, 1))
+        rates.append(q / (r / 1e3))
+    bt.close()
+    for mm in models:
+        mm.set_form("fp32")
+    fp32_ms = statistics.mean(timed(loop, 3, 1))
+    for mm in models:
+        mm.set_form(form)
+
+    # accuracy on sampled events against the FP64 oracle
+    picks = [0, 6, 7, 11, 50, 99]
+    acc = []
+    for k in picks:
+        idx = np.random.default_rng(k).choice(Qs[k], min(256, Qs[k]), replace=False)
+        ref = oracle.Model.from_event(evs[k]).loglike(th[k][idx], ex[k][idx])
+        acc.append(float(np.abs(got[k][idx].astype(np.float64) - ref).max()))
+
+    # roofline of the batched kernel: sum over events of 2 Q (N + P) K
+    hbm, bf16, bf16s, src = _peaks()
+    flops = sum(2.0 * sp.Q * (sp.N + 5) * sp.K for sp in specs)
+    kms = statistics.mean(kern)
+    achieved = flops / (kms / 1e3) / 1e12
+    roof = {"bound": "tensor", "peak": bf16, "unit": "TFLOP/s",
+            "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate)",
+            "achieved": round(achieved, 2), "frac": round(achieved / bf16, 4),
+            "traffic": _traffic_from_profile("tc_batch_kernel", [
+                "paper_2508_04172_gb300/csrc/mf_tc.cu", "paper_2508_04172_gb300/csrc/mf_epilogue.cuh"]),
+            "kernel": "tc_batch_kernel", "algorithmic_flops_per_launch": flops,
+            "kernel_ms": round(kms, 4)}
+
+    # end to end: host buffers in, results out, through the batch call
+    h_th = [torch.from_numpy(a).pin_memory() for a in th]
+    h_ex = [torch.from_numpy(b).pin_memory() for b in ex]
+    h_out = [torch.empty(q, dtype=torch.float32).pin_memory() for q in Qs]
+    bt = mf.Batch(models, Qs, autotune=True)
+
+    def e2e_step():
+        for a, ha in zip(d_th, h_th):
+            a.copy_(ha, non_blocking=True)
+        for b, hb in zip(d_ex, h_ex):
+            b.copy_(hb, non_blocking=True)
+        bt.loglike(d_th, d_ex, outs)
+        for o, ho in zip(outs, h_out):
+            ho.copy_(o, non_blocking=True)
+    e2e_ms = statistics.mean(timed(e2e_step, max(3, args.steps // 2), 2))
+    bt.close()
+    bi = sum(a.size * 4 + b.size * 4 for a, b in zip(th, ex))
+    value = Qtot * world / (ms / 1e3)
+    line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16x3",
+            "data": "synthetic (seeded closed-form stand-in overlaps)",
+            "config": {"workload": f"C3: {len(specs)} events, 3 det x 4 modes, N {min(sp.N for sp in specs)}"
+                                   f"..{max(sp.N for sp in specs)}, rank {min(sp.rank for sp in specs)}.."
+                                   f"{max(sp.rank for sp in specs)}, Q {min(Qs)}..{max(Qs)} "
+                                   f"(total {Qtot}) per step per GPU",
+                       "form": form, "l2": "flushed before every timed step (256 MB write)",
+                       "launch": f"one persistent tcgen05 launch + combine, CUDA graph replay; "
+                                 f"tuned shape: {shape[0]} passes (= CTAs per cluster), "
+                                 f"weight ring {shape[1]}, {shape[2]} clusters",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": round(Qtot * world / (e2e_ms / 1e3), 1), "unit": "evals/s",
+                    "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": Qtot * 4,
+                    "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": 2 * args.steps,
+            "clocks": ck,
+            "status": status,
+            "batch_vs_separate_calls": {"separate_ms": round(loop_ms, 4),
+                                        "speedup": round(loop_ms / ms, 3), "bitwise_equal": bool(same)},
+            "speedup_vs_plain_fp32": round(fp32_ms / ms, 3),
+            "plain_fp32_separate_ms": round(fp32_ms, 3),
+            "per_event_alone_evals_per_s": {"min": round(min(rates), 1),
+                                            "median": round(statistics.median(rates), 1),
+                                            "max": round(max(rates), 1)},
+            "accuracy": {"max_abs_dlnl_sampled_events": max(acc), "per_event": acc,
+                         "events": picks, "n_checked_per_event": 256},
+            "autotune": {"table_passes_ring_ms": table, "seconds": round(tune_s, 2)},
+            "build_seconds": round(build_s, 1)}
+    if rank == 0 and world == 1:
+        _, _, n, rate, cores = oracle_baseline(evs[0], th[0], ex[0], budget_s=args.cpu_budget)
+        line["cpu_baseline"] = {"value": round(rate, 1), "unit": "evals/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": f"first {n} queries of event 0 of the C3 batch "
+                                          f"(N={specs[0].N}, rank {specs[0].rank}), FP64 C + OpenMP"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
 def run_reference(args):
     rank, world, _ = _dist()
     if rank != 0:
         return
     import oracle
-    from workload.standin import make_event, make_queries, spec_for
-    spec = spec_for(args.config)
+    from workload.standin import c3_specs, make_event, make_queries, spec_for
+    # C3: the oracle on the batch's first event (events are evaluated alike)
+    spec = c3_specs()[0] if args.config == "C3" else spec_for(args.config)
     ev = make_event(spec)
     om = oracle.Model.from_event(ev)
     th, ex = make_queries(ev, spec.Q, seed=spec.seed + 17)
@@ -380,19 +607,26 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="C1", choices=["C0", "C1", "C2", "C4"])
-    ap.add_argument("--forms", default="fp32,fp16_3term,bf16_3term,fp16_wsplit,fp16,bf16")
+    ap.add_argument("--config", default="C1", choices=["C0", "C1", "C2", "C3", "C4"])
+    ap.add_argument("--forms", default=None,
+                    help="comma list; default all RBF forms (C4: fp32,fp16_3term,mlp)")
     ap.add_argument("--check", type=int, default=2048, help="queries checked against the oracle")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.forms is None:
+        args.forms = ("fp32,fp16_3term,mlp" if args.config == "C4"
+                      else "fp32,fp16_3term,bf16_3term,fp16_wsplit,fp16,bf16")
     if args.impl == "reference":
         run_reference(args)
     else:
         import paper_2508_04172_gb300 as mf
         mf.build()
-        run_ours(args)
+        if args.config == "C3":
+            run_batch(args)
+        else:
+            run_ours(args)
 
 
 if __name__ == "__main__":

@@ -522,6 +522,8 @@ int mf_query(const mf_handle *h, const char *key, double *value) {
     else if (k == "n_pass") *value = (double)h->passes.size();
     else if (k == "Kdev") *value = h->Kdev;
     else if (k == "form") *value = (double)h->form;
+    else if (k == "launches" && h->form == MF_FORM_MLP)
+        return mf::surrogate_query(h, k, value);
     else if (k == "launches")
         *value = 1.0 + (h->passes.size() > 1 ? 1.0 : 0.0);
     else if (k.compare(0, 9, "surrogate") == 0 || k == "fallback_rate")

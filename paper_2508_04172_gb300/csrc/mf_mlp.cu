@@ -563,6 +563,7 @@ struct mf_surrogate {
     int *d_count = nullptr;                       // number of them
     float *d_ci = nullptr, *d_ce = nullptr, *d_co = nullptr, *d_cpart = nullptr;   // compacted copies
     double fallback_rate = 0;
+    int last_launches = 0;                        // kernels launched by the last mf_loglike
 };
 
 namespace mf {
@@ -814,6 +815,7 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
     const int np = (int)h->passes.size();
     if (!s->gate && !force_net) {   // held-out gate failed: the RBF path serves everything
         s->fallback_rate = 1.0;
+        s->last_launches = np > 1 ? 2 : 1;
         int rc = ensure_infer(s, 1, Q, E, np);
         if (rc) return rc;
         rc = launch_fp32(h, intr, ext, Q, E, out, st, np > 1 ? s->d_cpart : nullptr);
@@ -827,6 +829,8 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
     int rc = ensure_infer(s, chunk, Q, E, np);
     if (rc) return rc;
     MF_CUDA(cudaMemsetAsync(s->d_count, 0, 8, st));
+    const int n_chunks = (Q + chunk - 1) / chunk;
+    s->last_launches = n_chunks * (1 + (m->L - 2) + 1 + (np > 1 ? 1 : 0));
     const RotParams rot = make_rot(h);
     const EpiParams epi = make_epi(h);
     for (int q0 = 0; q0 < Q; q0 += chunk) {
@@ -887,6 +891,7 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
     }
     sur_scatter_kernel<<<(nfb + 255) / 256, 256, 0, st>>>(s->d_list, s->d_count, s->d_co, out);
     MF_CUDA(cudaGetLastError());
+    s->last_launches += 3 + (np > 1 ? 1 : 0);
     return MF_OK;
 }
 
@@ -1069,6 +1074,7 @@ int surrogate_query(const mf_handle *h, const std::string &k, double *v) {
     else if (k == "surrogate_loss") *v = s->loss;
     else if (k == "surrogate_r_gate") *v = s->r_gate;
     else if (k == "surrogate_n_params") *v = (double)s->net->n_params;
+    else if (k == "launches") *v = s->last_launches;
     else return MF_E_INVAL;
     return MF_OK;
 }
