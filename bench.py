@@ -233,7 +233,7 @@ def run_ours(args):
         tth, _ = make_queries(ev, 100000, seed=spec.seed + 101)
         hth, hex_ = make_queries(ev, 10000, seed=spec.seed + 102)
         sur = m.train_surrogate(torch.from_numpy(tth).to(dev), torch.from_numpy(hth).to(dev),
-                                torch.from_numpy(hex_).to(dev), seed=1)
+                                torch.from_numpy(hex_).to(dev), steps=args.surrogate_steps, seed=1)
     for f in forms:
         try:
             m.set_form(f)
@@ -300,7 +300,8 @@ def run_ours(args):
         roof = {"bound": "tensor", "peak": bf16, "unit": "TFLOP/s",
                 "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate)"}
         tag, srcs = "tc_kernel", ["paper_2508_04172_gb300/csrc/mf_tc.cu",
-                                  "paper_2508_04172_gb300/csrc/mf_epilogue.cuh"]
+                                  "paper_2508_04172_gb300/csrc/mf_epilogue.cuh",
+                                  "paper_2508_04172_gb300/csrc/mf_ptx.cuh"]
     achieved = flops / (kms / 1e3) / 1e12
     roof.update(achieved=round(achieved, 2), frac=round(achieved / roof["peak"], 4),
                 traffic=_traffic_from_profile(tag, srcs), kernel=tag,
@@ -494,7 +495,8 @@ def run_batch(args):
             "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate)",
             "achieved": round(achieved, 2), "frac": round(achieved / bf16, 4),
             "traffic": _traffic_from_profile("tc_batch_kernel", [
-                "paper_2508_04172_gb300/csrc/mf_tc.cu", "paper_2508_04172_gb300/csrc/mf_epilogue.cuh"]),
+                "paper_2508_04172_gb300/csrc/mf_tc.cu", "paper_2508_04172_gb300/csrc/mf_epilogue.cuh",
+                "paper_2508_04172_gb300/csrc/mf_ptx.cuh"]),
             "kernel": "tc_batch_kernel", "algorithmic_flops_per_launch": flops,
             "kernel_ms": round(kms, 4)}
 
@@ -612,6 +614,8 @@ def main():
                     help="comma list; default all RBF forms (C4: fp32,fp16_3term,mlp)")
     ap.add_argument("--check", type=int, default=2048, help="queries checked against the oracle")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--surrogate-steps", type=int, default=0,
+                    help="training steps of the surrogate (0: library default, 20000)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
