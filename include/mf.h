@@ -357,6 +357,12 @@ MF_API int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_
  *                mf_loglike (read back with mf_query "kernel_ms"), 0 = off.
  *   "pass_max" : widest column pass (16..512, multiple of 16) the tcgen05
  *                forms may use; re-lays out the weights.
+ *   "tc_design": tcgen05 kernel design: 0 = thread-block clusters sharing
+ *                the RBF tile in shared memory; 1 = the RBF tile in tensor
+ *                memory, one CTA per column pass (passes <= 192 columns);
+ *                -1 (default) = 1 when the columns fit in one such pass,
+ *                else 0.  Re-lays out the weights; mf_query "tc_design"
+ *                reports the design in use.
  *   "tc_nbs"   : depth (2..4) of the weight-tile ring of the tcgen05 kernel;
  *                0 (default) = deepest that fits in shared memory.
  *   "pass_count": 0 (default) = as few column passes as "pass_max" allows;

@@ -225,10 +225,22 @@ int prepare_form(mf_handle *h, mf_form f) {
         return MF_OK;
     }
     free_form(h);
-    h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : 176;
     h->pass_count = is_tc_form(f) ? h->pass_count_user : 0;   // exact counts: tcgen05 forms only
-    int rc = build_layout(h);
-    if (rc) return rc;
+    // tcgen05 design: the TMEM design when asked for, or (automatic) when the
+    // columns fit in one pass of its width -- measured faster there
+    h->tc_tmem = false;
+    int rc;
+    if (is_tc_form(f) && (h->tc_design == 1 || (h->tc_design == -1 && h->pass_count <= 1))) {
+        h->pass_max = h->pass_max_user ? std::min(h->pass_max_user, tc2_pass_max()) : tc2_pass_max();
+        rc = build_layout(h);
+        if (rc == MF_OK) h->tc_tmem = h->tc_design == 1 || h->passes.size() == 1;
+        else if (h->tc_design == 1) return rc;
+    }
+    if (!h->tc_tmem) {
+        h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : 176;
+        rc = build_layout(h);
+        if (rc) return rc;
+    }
     MF_CUDA(cudaMalloc((void **)&h->d_user_of_dev, sizeof(int) * h->Kdev));
     MF_CUDA(cudaMemcpy(h->d_user_of_dev, h->user_of_dev.data(), sizeof(int) * h->Kdev,
                        cudaMemcpyHostToDevice));
@@ -429,8 +441,9 @@ int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int
         partial = h->d_partial;
     }
     if (h->timing) MF_CUDA(cudaEventRecord(h->ev0, st));
-    int rc = mf::is_tc_form(h->form) ? mf::launch_tc(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial)
-                                 : mf::launch_fp32(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial);
+    int rc = !mf::is_tc_form(h->form) ? mf::launch_fp32(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial)
+             : h->tc_tmem ? mf::launch_tc2(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial)
+                            : mf::launch_tc(h, intrinsic, extrinsic, Q, E, out_lnL, st, partial);
     if (rc) return rc;
     if (h->timing) MF_CUDA(cudaEventRecord(h->ev1, st));
     if (np > 1) return mf::launch_combine(partial, np, Q, out_lnL, st, h->d_bad);
@@ -480,9 +493,16 @@ int mf_set_option(mf_handle *h, const char *key, double value) {
         }
         return MF_OK;
     }
+    if (k == "tc_design") {
+        int v = (int)value;
+        if (v < -1 || v > 1) return MF_E_INVAL;
+        h->tc_design = v;
+        if (h->have_layout && mf::is_tc_form(h->form)) return mf::prepare_form(h, h->form);
+        return MF_OK;
+    }
     if (k == "tc_nbs") {
         int v = (int)value;
-        if (v != 0 && (v < 2 || v > 4)) return MF_E_INVAL;
+        if (v != 0 && (v < 2 || v > 6)) return MF_E_INVAL;
         h->tc_nbs = v;
         return MF_OK;
     }
@@ -522,6 +542,7 @@ int mf_query(const mf_handle *h, const char *key, double *value) {
     else if (k == "n_pass") *value = (double)h->passes.size();
     else if (k == "Kdev") *value = h->Kdev;
     else if (k == "form") *value = (double)h->form;
+    else if (k == "tc_design") *value = h->tc_tmem ? 1.0 : 0.0;
     else if (k == "launches" && h->form == MF_FORM_MLP)
         return mf::surrogate_query(h, k, value);
     else if (k == "launches")

@@ -144,6 +144,8 @@ struct mf_handle {
     bool timing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int tc_nbs = 0;                 // W ring depth of the tcgen05 kernel (0: automatic)
+    int tc_design = -1;             // -1: automatic; 0: cluster-shared Phi in smem; 1: Phi in TMEM
+    bool tc_tmem = false;           // the current layout runs the TMEM design
     int pass_max_user = 0;          // 0: form default
     int pass_count_user = 0;        // 0: as few passes as pass_max allows; else exactly this many
     int pass_count = 0;             // the value the current layout was built with (tcgen05 forms)
@@ -179,6 +181,9 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
               cudaStream_t st, float *partial);
 int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStream_t st,
                    unsigned long long *bad);
+int launch_tc2(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+               cudaStream_t st, float *partial);
+int tc2_pass_max();
 // batched tcgen05 launch (all events share form and mode count)
 int fill_tc_event(const mf_handle *h, TcEvent *out);
 size_t tc_smem_bytes(mf_form f, int np, int nbox_max, int sb);   // 0: does not fit
