@@ -106,8 +106,9 @@ class Clocks:
 
 
 def _traffic_from_profile(kernel_tag: str, src_files):
-    """Per-launch DRAM bytes from a committed ncu summary, if it was taken
-    on the current kernel source (sha256 prefix recorded in the summary)."""
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on
+    the current kernel source (sha256 prefix recorded in the summary) and on
+    the same workload (kernel_tag = "<kernel>@<workload>")."""
     h = hashlib.sha256()
     for f in src_files:
         h.update(open(os.path.join(ROOT, f), "rb").read())
@@ -233,7 +234,8 @@ def run_ours(args):
         tth, _ = make_queries(ev, 100000, seed=spec.seed + 101)
         hth, hex_ = make_queries(ev, 10000, seed=spec.seed + 102)
         sur = m.train_surrogate(torch.from_numpy(tth).to(dev), torch.from_numpy(hth).to(dev),
-                                torch.from_numpy(hex_).to(dev), steps=args.surrogate_steps, seed=1)
+                                torch.from_numpy(hex_).to(dev), steps=args.surrogate_steps, seed=1,
+                                r_gate=0.9)   # the radius both sets are drawn from
     for f in forms:
         try:
             m.set_form(f)
@@ -304,7 +306,7 @@ def run_ours(args):
                                   "paper_2508_04172_gb300/csrc/mf_ptx.cuh"]
     achieved = flops / (kms / 1e3) / 1e12
     roof.update(achieved=round(achieved, 2), frac=round(achieved / roof["peak"], 4),
-                traffic=_traffic_from_profile(tag, srcs), kernel=tag,
+                traffic=_traffic_from_profile(f"{tag}@{spec.name}", srcs), kernel=tag,
                 algorithmic_flops_per_launch=flops, kernel_ms=round(kms, 4))
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
@@ -494,7 +496,7 @@ def run_batch(args):
     roof = {"bound": "tensor", "peak": bf16, "unit": "TFLOP/s",
             "peak_source": f"{src} bf16 dense burst (fp16 has the same nominal rate)",
             "achieved": round(achieved, 2), "frac": round(achieved / bf16, 4),
-            "traffic": _traffic_from_profile("tc_batch_kernel", [
+            "traffic": _traffic_from_profile("tc_batch_kernel@C3", [
                 "paper_2508_04172_gb300/csrc/mf_tc.cu", "paper_2508_04172_gb300/csrc/mf_epilogue.cuh",
                 "paper_2508_04172_gb300/csrc/mf_ptx.cuh"]),
             "kernel": "tc_batch_kernel", "algorithmic_flops_per_launch": flops,

@@ -333,7 +333,8 @@ MF_API int mf_mlp_query(const mf_mlp *m, const char *key, double *value);
  * the median <= gate_median (defaults 0.1 and 0.01).  In MF_FORM_MLP,
  * mf_loglike then evaluates the network (chunks of 65536 queries: input
  * layer, hidden GEMMs, final GEMM fused with the lnL epilogue) and sends
- * queries with |x| beyond the largest training |x| to the FP32 RBF path
+ * queries with |x| beyond the training radius (r_gate; by default the
+ * largest training |x|) to the FP32 RBF path
  * (the call synchronises its stream once to size that launch); if the gate
  * failed, the RBF path serves every query.  mf_query: "fallback_rate",
  * "surrogate_gate", "surrogate_heldout_max" / "_median" / "_p99",
@@ -346,6 +347,7 @@ typedef struct mf_surrogate_params {
     int steps, batch, hidden, n_hidden;
     float lr, lr_min;
     float gate_max, gate_median;
+    float r_gate;              /* training radius in x; 0 = largest training |x| */
     unsigned long long seed;
 } mf_surrogate_params;
 MF_API int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train,

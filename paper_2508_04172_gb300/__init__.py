@@ -30,7 +30,7 @@ class SurrogateParams(ctypes.Structure):
     _fields_ = [("steps", ctypes.c_int), ("batch", ctypes.c_int), ("hidden", ctypes.c_int),
                 ("n_hidden", ctypes.c_int), ("lr", ctypes.c_float), ("lr_min", ctypes.c_float),
                 ("gate_max", ctypes.c_float), ("gate_median", ctypes.c_float),
-                ("seed", ctypes.c_ulonglong)]
+                ("r_gate", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
 
 
 class MlpTrainParams(ctypes.Structure):
@@ -254,12 +254,12 @@ class Interpolant:
 
     def train_surrogate(self, train_intrinsic, held_intrinsic, held_extrinsic, steps=0, batch=0,
                         hidden=0, n_hidden=0, lr=0.0, lr_min=0.0, gate_max=0.0, gate_median=0.0,
-                        seed=0, stream=None):
+                        seed=0, r_gate=0.0, stream=None):
         """mf_train_surrogate with device tensors [n,4] (train) and [m,4], [m,E]
         (held out); zero arguments take the library defaults.  Returns the
         held-out statistics."""
         p = SurrogateParams(int(steps), int(batch), int(hidden), int(n_hidden), float(lr),
-                            float(lr_min), float(gate_max), float(gate_median), int(seed))
+                            float(lr_min), float(gate_max), float(gate_median), float(r_gate), int(seed))
         P = ctypes.c_void_p
         _check(lib().mf_train_surrogate(self._h, P(train_intrinsic.data_ptr()),
                                         train_intrinsic.shape[0], P(held_intrinsic.data_ptr()),

@@ -217,7 +217,12 @@ int prepare_form(mf_handle *h, mf_form f) {
     if (f == MF_FORM_MLP) {
         // the surrogate serves through the FP32 layout; its FP32 weights are the fallback
         if (!h->sur) return MF_E_STATE;
+        // 128-column passes: the surrogate's final GEMM then allocates 128 TMEM
+        // columns per CTA and several CTAs share an SM (its epilogue is
+        // latency-bound); the FP32 fallback runs on the same layout
+        h->fp32_pass_max = 128;
         int rc = prepare_form(h, MF_FORM_FP32);
+        h->fp32_pass_max = 176;
         if (rc) return rc;
         rc = surrogate_prepare(h);
         if (rc) return rc;
@@ -237,7 +242,7 @@ int prepare_form(mf_handle *h, mf_form f) {
         else if (h->tc_design == 1) return rc;
     }
     if (!h->tc_tmem) {
-        h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : 176;
+        h->pass_max = is_tc_form(f) ? (h->pass_max_user ? h->pass_max_user : 256) : h->fp32_pass_max;
         rc = build_layout(h);
         if (rc) return rc;
     }

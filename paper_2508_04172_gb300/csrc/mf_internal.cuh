@@ -149,6 +149,7 @@ struct mf_handle {
     int pass_max_user = 0;          // 0: form default
     int pass_count_user = 0;        // 0: as few passes as pass_max allows; else exactly this many
     int pass_count = 0;             // the value the current layout was built with (tcgen05 forms)
+    int fp32_pass_max = 176;        // widest FP32 pass (the surrogate form lays out narrower passes)
     unsigned gen = 0;               // bumped whenever the device layout or weights change
     // tcgen05 forms: tensor maps (opaque 128-byte CUtensorMap) of W_hi / W_lo
     alignas(64) unsigned char tmap_hi[128];

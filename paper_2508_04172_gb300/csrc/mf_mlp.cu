@@ -114,6 +114,9 @@ int make_plan(GemmPlan &pl, int epi, const void *A, int M, int K, const void *B,
 }
 
 int nt_for(int n) { return std::min(256, (n + 15) / 16 * 16); }
+// Column tile of the hidden-layer GEMMs (N = hidden): 128 columns keep three
+// CTAs (128 TMEM columns each) per SM, so more epilogue warps hide latency.
+int nt_hidden(int n) { return std::min(128, (n + 15) / 16 * 16); }
 
 LayerTab layer_tab(const mf_mlp *m) {
     LayerTab t;
@@ -192,7 +195,7 @@ int build_train_plans(mf_mlp *m, int rows) {
         g.out_t = m->Hts[l];
         g.out_f = m->Zs[l];
         GemmPlan pl;
-        rc = make_plan(pl, EPI_SILU, m->Hs[l - 1], rows, H, m->W[l], H, nt_for(H), g, m->d_err);
+        rc = make_plan(pl, EPI_SILU, m->Hs[l - 1], rows, H, m->W[l], H, nt_hidden(H), g, m->d_err);
         if (rc) return rc;
         m->fwd.push_back(pl);
     }
@@ -235,7 +238,7 @@ int build_train_plans(mf_mlp *m, int rows) {
                 g.out_f = m->dZ0;
             }
             GemmPlan pl;
-            rc = make_plan(pl, EPI_DSILU, dz, rows, m->out[l], m->Wt[l], m->in[l], nt_for(m->in[l]), g,
+            rc = make_plan(pl, EPI_DSILU, dz, rows, m->out[l], m->Wt[l], m->in[l], nt_hidden(m->in[l]), g,
                            m->d_err);
             if (rc) return rc;
             m->bwd.push_back(pl);
@@ -404,7 +407,7 @@ int mf_mlp_forward(mf_mlp *m, const float *X, int B, float *Y, void *stream) {
             rc = make_plan(pl, EPI_F32, m->Hs[l - 1], B, H, m->W[l], m->n_out, nt_for(m->n_out), g, m->d_err);
         } else {
             g.out_bf = m->Hs[l];
-            rc = make_plan(pl, EPI_SILU, m->Hs[l - 1], B, H, m->W[l], H, nt_for(H), g, m->d_err);
+            rc = make_plan(pl, EPI_SILU, m->Hs[l - 1], B, H, m->W[l], H, nt_hidden(H), g, m->d_err);
         }
         if (rc) return rc;
         rc = launch_plan(pl, st);
@@ -543,7 +546,7 @@ struct mf_surrogate {
     mf_mlp *net = nullptr;
     int K = 0, K_out = 0;                 // user columns, network outputs (K rounded to 8)
     double *d_mu = nullptr, *d_s = nullptr;   // per user column: mean, scale of the targets
-    float r_gate = 0.f;                   // largest |x| of the training set
+    float r_gate = 0.f;                   // training radius: queries beyond it use the RBF path
     bool gate = false;                    // held-out gate passed
     double ho_max = 0, ho_median = 0, ho_p99 = 0;
     float train_ms = 0, label_ms = 0, gate_ms = 0, loss = 0;
@@ -673,14 +676,21 @@ __global__ void sur_devweights_kernel(const float *__restrict__ WL, const float 
 }
 
 // Network input layer for lnL queries: x = R (theta - centre) (FP32, as the
-// RBF path), first layer -> H1; flags queries with |x| > r_gate.
-__global__ void sur_input_kernel(const float *__restrict__ th, int Q, const RotParams rot,
+// RBF path), first layer -> H1 (one thread per query, the H outputs written
+// as 16-byte vectors); flags queries with |x| > r_gate.
+__global__ void __launch_bounds__(128) sur_input_kernel(const float *__restrict__ th, int Q, const RotParams rot,
                                  const float *__restrict__ W1, const float *__restrict__ b1, int H,
                                  __nv_bfloat16 *__restrict__ H1, float r_gate, unsigned char *__restrict__ flag,
                                  int *__restrict__ count) {
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)Q * H) return;
-    const int q = (int)(idx / H), o = (int)(idx % H);
+    __shared__ float4 w[256];     // [H] rows of W1 (4 inputs)
+    __shared__ float bb[256];
+    for (int o = threadIdx.x; o < H; o += blockDim.x) {
+        w[o] = make_float4(W1[4 * o], W1[4 * o + 1], W1[4 * o + 2], W1[4 * o + 3]);
+        bb[o] = b1[o];
+    }
+    __syncthreads();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= Q) return;
     const float4 t = *reinterpret_cast<const float4 *>(th + (size_t)q * 4);
     const float d[4] = {t.x - rot.centre[0], t.y - rot.centre[1], t.z - rot.centre[2], t.w - rot.centre[3]};
     float x[4], r2 = 0.f;
@@ -689,11 +699,26 @@ __global__ void sur_input_kernel(const float *__restrict__ th, int Q, const RotP
         x[a] = rot.R[4 * a] * d[0] + rot.R[4 * a + 1] * d[1] + rot.R[4 * a + 2] * d[2] + rot.R[4 * a + 3] * d[3];
         r2 = fmaf(x[a], x[a], r2);
     }
-    float z = b1[o];
+    uint4 *row = reinterpret_cast<uint4 *>(H1 + (size_t)q * H);
+    for (int o0 = 0; o0 < H; o0 += 8) {
+        float v[8];
 #pragma unroll
-    for (int a = 0; a < 4; ++a) z = fmaf(W1[o * 4 + a], x[a], z);
-    H1[idx] = __float2bfloat16_rn(silu_f(z));
-    if (o == 0 && flag) {
+        for (int e = 0; e < 8; ++e) {
+            const float4 ww = w[o0 + e];
+            float z = fmaf(ww.x, x[0], bb[o0 + e]);
+            z = fmaf(ww.y, x[1], z);
+            z = fmaf(ww.z, x[2], z);
+            z = fmaf(ww.w, x[3], z);
+            v[e] = silu_f(z);
+        }
+        uint4 p;
+        p.x = Half2<1>::pack(v[0], v[1]);
+        p.y = Half2<1>::pack(v[2], v[3]);
+        p.z = Half2<1>::pack(v[4], v[5]);
+        p.w = Half2<1>::pack(v[6], v[7]);
+        row[o0 / 8] = p;
+    }
+    if (flag) {
         const bool out = !(sqrtf(r2) <= r_gate);
         flag[q] = out;
         if (out) atomicAdd(count, 1);
@@ -835,8 +860,7 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
     const EpiParams epi = make_epi(h);
     for (int q0 = 0; q0 < Q; q0 += chunk) {
         const int Qc = std::min(chunk, Q - q0);
-        const long long n1 = (long long)Qc * H;
-        sur_input_kernel<<<(unsigned)((n1 + 255) / 256), 256, 0, st>>>(
+        sur_input_kernel<<<(unsigned)((Qc + 127) / 128), 128, 0, st>>>(
             intr + (size_t)q0 * 4, Qc, rot, m->d_p, m->d_p + H * 4, H, s->d_h[0], force_net ? 1e30f : s->r_gate,
             s->d_flag + q0, s->d_count);
         MF_CUDA(cudaGetLastError());
@@ -846,7 +870,7 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
             g.bias = m->d_p + m->off[l] + H * H;
             g.out_bf = s->d_h[cur ^ 1];
             GemmPlan pl;
-            rc = make_plan(pl, EPI_SILU, s->d_h[cur], Qc, H, m->W[l], H, nt_for(H), g, h->d_err);
+            rc = make_plan(pl, EPI_SILU, s->d_h[cur], Qc, H, m->W[l], H, nt_hidden(H), g, h->d_err);
             if (rc) return rc;
             rc = launch_plan(pl, st);
             if (rc) return rc;
@@ -998,7 +1022,7 @@ int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train, 
     {
         std::vector<float> r(n_train);
         cudaMemcpy(r.data(), rad, 4 * (size_t)n_train, cudaMemcpyDeviceToHost);
-        s->r_gate = *std::max_element(r.begin(), r.end());
+        s->r_gate = sp->r_gate > 0 ? sp->r_gate : *std::max_element(r.begin(), r.end());
     }
     // ---- training
     mf_mlp_train_params tp{};

@@ -44,9 +44,12 @@ struct GemmArgs {
     float *partial;           // [n_pass][M]
 };
 
-__device__ __forceinline__ float silu_f(float z) { return z / (1.f + __expf(-z)); }
+// SiLU(z) = z sigmoid(z), sigmoid(z) = 1 / (1 + 2^(-z log2 e)); the fast
+// exp2 and division keep ~2^-21 relative accuracy, far below BF16 rounding.
+__device__ __forceinline__ float sigmoid_f(float z) { return __fdividef(1.f, 1.f + ex2(-1.4426950408889634f * z)); }
+__device__ __forceinline__ float silu_f(float z) { return z * sigmoid_f(z); }
 __device__ __forceinline__ float silu_grad_f(float z) {
-    const float s = 1.f / (1.f + __expf(-z));
+    const float s = sigmoid_f(z);
     return s * (1.f + z * (1.f - s));
 }
 
@@ -189,11 +192,24 @@ gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUte
                             in[e] = (mv && n + e < g.N) ? g.aux[(size_t)m * g.N + n + e] : 0.f;
                     }
                 }
+                float bias16[16];
+                if (g.bias && n + 16 <= g.N && ((reinterpret_cast<uintptr_t>(g.bias + n) & 15) == 0)) {
+                    const float4 *bp = reinterpret_cast<const float4 *>(g.bias + n);
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const float4 b4 = __ldg(bp + q4);
+                        bias16[4 * q4] = b4.x; bias16[4 * q4 + 1] = b4.y;
+                        bias16[4 * q4 + 2] = b4.z; bias16[4 * q4 + 3] = b4.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) bias16[e] = (g.bias && n + e < g.N) ? __ldg(g.bias + n + e) : 0.f;
+                }
                 float r[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const bool valid = mv && n + e < g.N;
-                    const float bs = (g.bias && n + e < g.N) ? __ldg(g.bias + n + e) : 0.f;
+                    const float bs = bias16[e];
                     float o;
                     if (EPI == EPI_SILU) {
                         o = silu_f(v[e] + bs);

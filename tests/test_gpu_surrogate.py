@@ -79,7 +79,9 @@ def test_queries_beyond_training_radius_use_rbf(c4):
     finally:
         m.set_form("fp32")
     assert rate == pytest.approx(far.mean(), abs=2e-3)
-    assert np.array_equal(got[far], ref[far])
+    # the same FP32 RBF kernel; the surrogate form lays the columns out in
+    # narrower passes, so only the grouping of the passes' partial sums differs
+    assert np.abs(got[far] - ref[far]).max() <= 1e-5 * max(1.0, np.abs(ref[far]).max())
     assert np.abs(got[~far] - ref[~far]).max() <= 0.1
 
 
