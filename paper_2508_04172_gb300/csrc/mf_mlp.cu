@@ -78,7 +78,7 @@ int launch_plan_epi(const GemmPlan &pl, const EpiParams &epi, int nm, cudaStream
     }
     MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     void *args[4] = {(void *)&pl.ta, (void *)&pl.tb, (void *)&pl.g, (void *)&epi};
-    MF_CUDA(cudaLaunchKernel(kern, grid, dim3(kGemmThreads), args, smem, st));
+    MF_CUDA(cudaLaunchKernel(kern, grid, dim3(EPI == EPI_LNL ? kGemmThreadsLnl : kGemmThreads), args, smem, st));
     return MF_OK;
 }
 

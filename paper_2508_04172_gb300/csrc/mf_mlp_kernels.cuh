@@ -13,6 +13,7 @@ namespace {   // kernels and launch plans are private to the including unit
 
 constexpr int kGemmStages = 4;
 constexpr int kGemmThreads = 192;          // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int kGemmThreadsLnl = 320;       // lnL epilogue: warps 2..9, two per TMEM lane quadrant
 constexpr int kGemmATile = kTile * kRowBytes;
 constexpr int kMlpMaxLayers = 8;
 constexpr int kMlpMaxIn = 16;
@@ -64,7 +65,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // inputs, FP32 accumulator in TMEM); four warps read the accumulator rows
 // (thread = row) and apply the epilogue.
 template <int EPI, int NM>
-__global__ void __launch_bounds__(kGemmThreads)
+__global__ void __launch_bounds__(EPI == EPI_LNL ? kGemmThreadsLnl : kGemmThreads)
 gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB,
             const __grid_constant__ GemmArgs g, const __grid_constant__ EpiParams epi) {
     extern __shared__ uint8_t smem_raw[];
@@ -75,6 +76,7 @@ gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUte
     uint64_t *empty = full + kGemmStages;
     uint64_t *tfull = empty + kGemmStages;
     uint32_t *tslot = (uint32_t *)(tfull + 1);
+    float *red = (float *)((uint8_t *)full + 128);            // [128] lnL of the second warp half
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kTile;
     int n0, nw;
@@ -155,14 +157,28 @@ gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUte
         ok = __all_sync(0xffffffffu, ok);
         tc_fence_after();
         const uint32_t tb = tmem + ((uint32_t)(quad * 32) << 16);
-        if (ok && EPI == EPI_LNL) {
-            const Pass ps = epi.passes[blockIdx.y];
-            const QueryExt x = load_ext(epi, g.ext, g.E, min(m, g.M - 1));
-            TmemAcc<true> acc{tb, nullptr, g.bias + ps.col0};
-            bool bad = false;
-            float l = pass_lnl<NM>(epi, ps, x, acc, bad);
-            if (bad) l = __int_as_float(0x7fc00000);
-            if (mv) {
+        if (EPI == EPI_LNL) {
+            // two warps per lane quadrant: each takes one contiguous half of the
+            // pass's column groups (lnL is a sum over groups), the halves meet
+            // in shared memory
+            const int half = (warp - 2) >> 2;
+            Pass ps = epi.passes[blockIdx.y];
+            const int n_first = (ps.ng + 1) / 2;
+            if (half == 0) ps.ng = n_first;
+            else { ps.g0 += n_first; ps.ng -= n_first; }
+            float l = 0.f;
+            if (ok && ps.ng > 0) {
+                const QueryExt x = load_ext(epi, g.ext, g.E, min(m, g.M - 1));
+                TmemAcc<true> acc{tb, nullptr, g.bias + epi.passes[blockIdx.y].col0};
+                bool bad = false;
+                l = pass_lnl<NM>(epi, ps, x, acc, bad);
+                if (bad) l = __int_as_float(0x7fc00000);
+            }
+            if (!ok) l = __int_as_float(0x7fc00000);
+            if (half == 1) red[row] = l;
+            asm volatile("bar.sync 1, 256;" ::: "memory");
+            if (half == 0 && mv) {
+                l += red[row];
                 if (gridDim.y == 1) {
                     g.lnl_out[m] = l;
                     if (l != l) atomicAdd(epi.bad, 1ull);
@@ -282,7 +298,10 @@ gemm_kernel(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUte
 }
 
 inline size_t gemm_smem_bytes(int NT) {
-    return 1024 + (size_t)kGemmStages * (kGemmATile + NT * kRowBytes) + (2 * kGemmStages + 1) * 8 + 16;
+    // barriers and the TMEM slot in the first 128 bytes after the ring, then
+    // the 128-float exchange of the split lnL epilogue
+    static_assert((2 * kGemmStages + 1) * 8 + 4 <= 128, "barriers overflow their 128 bytes");
+    return 1024 + (size_t)kGemmStages * (kGemmATile + NT * kRowBytes) + 128 + 128 * sizeof(float);
 }
 
 // One GEMM launch, prepared once: operand tensor maps and arguments.
