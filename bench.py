@@ -48,6 +48,28 @@ def _peaks():
         return 6800.0, 1900.0, 1700.0, "fallback"
 
 
+def _rank_seed(base_seed: int, rank: int) -> int:
+    """Query seed of a replica: every rank evaluates its own batch."""
+    return base_seed + 17 + 1000 * rank
+
+
+def _max_over_ranks(x: float, device=None) -> float:
+    """The slowest rank's value (the job's step time); x itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64,
+                     device=device if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(units_per_rank: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed / the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -134,7 +156,7 @@ def build_workload(cfg: str, rank: int):
                                      standin.standin_sigma(ev, ev.nodes), spec.rank, spec.eps,
                                      spec.modes, ev.det, spec.t0, spec.dt, spec.d_ref, ev.metric,
                                      ev.centre, spec.tail_degree, "fp32")
-    th, ex = make_queries(ev, spec.Q, seed=spec.seed + 17 + 1000 * rank)
+    th, ex = make_queries(ev, spec.Q, seed=_rank_seed(spec.seed, rank))
     return spec, ev, m, th, ex
 
 
@@ -271,22 +293,15 @@ def run_ours(args):
     ok = [f for f in forms if "error" not in res[f] and res[f]["max_abs_dlnl"] <= TOL and f != "mlp"]
     plain = "fp32"
     chosen = min(ok, key=lambda f: res[f]["ms_per_step"]) if ok else plain
-    ms = res[chosen]["ms_per_step"]
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = Q * world / (ms / 1e3)
+    ms = _max_over_ranks(res[chosen]["ms_per_step"], dev)
+    value = _job_rate(Q, world, ms)
 
     # end to end through the C ABI with pinned host buffers
     h_th = torch.from_numpy(th).pin_memory()
     h_ex = torch.from_numpy(ex).pin_memory()
     h_out = torch.empty(Q, dtype=torch.float32).pin_memory()
     e2e_ms, bi, bo = time_e2e(m, chosen, h_th, h_ex, h_out, args.steps, args.warmup, dev)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = _max_over_ranks(e2e_ms, dev)
 
     # roofline of the dominant kernel (the fused lnL kernel of the chosen form)
     hbm, bf16, bf16s, src = _peaks()
@@ -322,7 +337,7 @@ def run_ours(args):
                        "form": chosen, "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
-            "e2e": {"value": round(Q * world / (e2e_ms / 1e3), 1), "unit": "evals/s",
+            "e2e": {"value": round(_job_rate(Q, world, e2e_ms), 1), "unit": "evals/s",
                     "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                     "ms_per_step": round(e2e_ms, 4)},
             "gpu_launches": int(res[chosen]["launches"]),
@@ -398,7 +413,7 @@ def run_batch(args):
             ev.nodes, standin.node_overlaps(ev), standin.standin_sigma(ev, ev.nodes), sp.rank,
             sp.eps, sp.modes, ev.det, sp.t0, sp.dt, sp.d_ref, ev.metric, ev.centre, sp.tail_degree,
             form))
-        a, b = make_queries(ev, sp.Q, seed=sp.seed + 17 + 1000 * rank)
+        a, b = make_queries(ev, sp.Q, seed=_rank_seed(sp.seed, rank))
         evs.append(ev)
         th.append(a)
         ex.append(b)
@@ -455,11 +470,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     ck = clocks.summary()
     bt.set_option("timing", 0)
-    ms = statistics.mean(ts)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _max_over_ranks(statistics.mean(ts), dev)
     status = bt.sync_status()[0]
     got = [o.cpu().numpy() for o in outs]
 
@@ -516,10 +527,10 @@ def run_batch(args):
         bt.loglike(d_th, d_ex, outs)
         for o, ho in zip(outs, h_out):
             ho.copy_(o, non_blocking=True)
-    e2e_ms = statistics.mean(timed(e2e_step, max(3, args.steps // 2), 2))
+    e2e_ms = _max_over_ranks(statistics.mean(timed(e2e_step, max(3, args.steps // 2), 2)), dev)
     bt.close()
     bi = sum(a.size * 4 + b.size * 4 for a, b in zip(th, ex))
-    value = Qtot * world / (ms / 1e3)
+    value = _job_rate(Qtot, world, ms)
     line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16x3",
@@ -534,7 +545,7 @@ def run_batch(args):
                                  f"weight ring {shape[1]}, {shape[2]} clusters",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
-            "e2e": {"value": round(Qtot * world / (e2e_ms / 1e3), 1), "unit": "evals/s",
+            "e2e": {"value": round(_job_rate(Qtot, world, e2e_ms), 1), "unit": "evals/s",
                     "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": Qtot * 4,
                     "ms_per_step": round(e2e_ms, 4)},
             "gpu_launches": 2 * args.steps,
