@@ -322,3 +322,31 @@ def test_face_on_22_is_circular_under_polarisation_angle(hm_model):
             dphi = np.angle(c / c0)
             assert min(abs(np.exp(1j * dphi) - np.exp(2j * psi)),
                        abs(np.exp(1j * dphi) - np.exp(-2j * psi))) < 1e-12
+
+
+def test_lnl_from_columns_at_nodes_matches_standin(oracle_mod):
+    """oracle.loglike_columns (lnL from supplied interpolated columns, the
+    judge of the surrogate) given the exact node values at a node reproduces
+    the analytic stand-in lnL a X - a^2 Y (no RBF evaluation and no FP32
+    rounding of theta involved, hence the tight bound), and given the RBF
+    evaluation of a query it reproduces the full oracle lnL."""
+    ev, m = _zero_delay_model(oracle_mod, "C1", 300)
+    s = ev.spec
+    rng = np.random.default_rng(9)
+    ext = np.array([[150.0, -0.4, 2.1, 0.7, 0.0]], np.float32)
+    a = 100.0 / 150.0
+    for idx in rng.choice(s.N, 4, replace=False):
+        y = ev.nodes[idx]
+        sig = standin.standin_sigma(ev, y[None])[:, 0]
+        X = Y = 0.0
+        for k in range(s.n_det):
+            c1 = m.amplitudes(k, 100.0, float(ext[0, 1]), float(ext[0, 2]), float(ext[0, 3]))
+            z = np.array([standin.standin_z(ev, k, j, y[None], np.array([0.0]))[0, 0]
+                          for j in range(s.n_modes)])
+            X += np.real(np.vdot(c1, z))
+            Y += 0.5 * np.real(np.vdot(c1, sig[k] @ c1))
+        got = oracle_mod.loglike_columns(m, m.F[idx][None], ext)[0]
+        assert abs(got - (a * X - a * a * Y)) < 1e-8 * (1 + abs(a * X) + abs(a * a * Y))
+    th, ex = make_queries(ev, 50, seed=91)
+    F = m.rbf_eval(m.rotate(th.astype(np.float64)))
+    assert np.allclose(oracle_mod.loglike_columns(m, F, ex), m.loglike(th, ex), rtol=0, atol=1e-9)
