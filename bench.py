@@ -605,7 +605,7 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded closed-form stand-in overlaps)",
-            "config": {"workload": f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, "
+            "config": {"workload": ("C3 (event 0 of the 100-event batch) " if args.config == "C3" else "") + f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, "
                                    f"N={spec.N} nodes, rank {spec.rank}, M={spec.M}, K={spec.K}",
                        "form": "fp64 CPU oracle", "parallelism": "host cores"},
             "cpu_baseline": {"value": round(v, 1), "unit": "evals/s", "cores": oracle.num_threads(),
