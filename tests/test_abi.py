@@ -47,3 +47,41 @@ def test_invalid_arguments_are_rejected_before_any_device_work():
     assert L.mf_loglike(None, None, None, 16, 5, None, None) == -1
     assert L.mf_set_form(None, 0) == -1
     assert L.mf_svd_compress(None, 4, 4, 2, None, None, None, None) == -1
+
+
+def test_batch_network_and_surrogate_entry_points_reject_bad_arguments():
+    """The batched-events, network and surrogate entry points validate their
+    arguments on the host before any device work."""
+    L = mf.lib()
+    P = ctypes.c_void_p
+    out = P()
+    q = (ctypes.c_int * 1)(16)
+    # batched events: no handles, empty or oversized batches, NULL plan / output
+    assert L.mf_batch_create(None, 1, q, 0, None, ctypes.byref(out)) == mf.MF_E_INVAL
+    assert L.mf_batch_create(None, 0, q, 0, None, ctypes.byref(out)) == mf.MF_E_INVAL
+    assert L.mf_batch_create(None, 129, q, 0, None, ctypes.byref(out)) == mf.MF_E_INVAL
+    assert L.mf_batch_create(None, 1, q, 0, None, None) == mf.MF_E_INVAL
+    assert L.mf_batch_loglike(None, None, None, q, 5, None, None) == mf.MF_E_INVAL
+    assert L.mf_batch_set_option(None, b"graph", 0.0) == mf.MF_E_INVAL
+    v = ctypes.c_double()
+    assert L.mf_batch_query(None, b"n_pass", ctypes.byref(v)) == mf.MF_E_INVAL
+    assert L.mf_batch_tuning(None, 0, None, None, None) == mf.MF_E_INVAL
+    L.mf_batch_free(None)                          # no-op
+    # network: every dimension limit of mf_mlp_create
+    for dims in ((0, 256, 3, 656), (17, 256, 3, 656), (4, 8, 3, 656), (4, 100, 3, 656),
+                 (4, 272, 3, 656), (4, 256, 0, 656), (4, 256, 8, 656), (4, 256, 3, 650),
+                 (4, 256, 3, 0)):
+        assert L.mf_mlp_create(*dims, 0, ctypes.byref(out)) == mf.MF_E_INVAL, dims
+    assert L.mf_mlp_create(4, 256, 3, 656, 0, None) == mf.MF_E_INVAL
+    assert L.mf_mlp_n_params(None) == -1
+    assert L.mf_mlp_set_params(None, None) == mf.MF_E_INVAL
+    assert L.mf_mlp_forward(None, None, 16, None, None) == mf.MF_E_INVAL
+    assert L.mf_mlp_gradient(None, None, None, 16, None, None, None) == mf.MF_E_INVAL
+    assert L.mf_mlp_query(None, b"loss", ctypes.byref(v)) == mf.MF_E_INVAL
+    L.mf_mlp_free(None)
+    # surrogate training: no handle / no data / no parameters
+    sp = mf.SurrogateParams()
+    assert L.mf_train_surrogate(None, None, 1000, None, None, 0, 5, ctypes.byref(sp), None) == mf.MF_E_INVAL
+    # the no-allocation path and the column evaluation reject NULL handles too
+    assert L.mf_loglike_noalloc(None, None, None, 16, 5, None, None) == mf.MF_E_INVAL
+    assert L.mf_eval_columns(None, None, 16, None, None) == mf.MF_E_INVAL
