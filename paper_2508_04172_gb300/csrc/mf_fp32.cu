@@ -71,11 +71,11 @@ fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q
     }
 
     const int tq = tid >> 4, tc = tid & 15;
-    float acc[8][kJMax];
+    float2 acc[4][kJMax];      // rows (2h, 2h+1) of this thread, packed for fma.rn.f32x2
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < kJMax; ++j) acc[i][j] = 0.f;
+        for (int j = 0; j < kJMax; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
     const int wq = tid & (kTile - 1);          // query handled when filling phi
     const int wn0 = (tid >> 7) * (kChunk / 2); // 16 nodes per thread
@@ -118,14 +118,17 @@ fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q
         for (int n = 0; n < kChunk; ++n) {
             float4 p0 = *reinterpret_cast<const float4 *>(phi_s + n * kTile + tq * 8);
             float4 p1 = *reinterpret_cast<const float4 *>(phi_s + n * kTile + tq * 8 + 4);
-            float p[8] = {p0.x, p0.y, p0.z, p0.w, p1.x, p1.y, p1.z, p1.w};
+            const float2 p[4] = {make_float2(p0.x, p0.y), make_float2(p0.z, p0.w), make_float2(p1.x, p1.y),
+                                 make_float2(p1.z, p1.w)};
             float wv[kJMax];
 #pragma unroll
             for (int j = 0; j < kJMax; ++j) wv[j] = (j < jw) ? w_s[n * width + tc + 16 * j] : 0.f;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
+            for (int j = 0; j < kJMax; ++j) {
+                const float2 w2 = make_float2(wv[j], wv[j]);
 #pragma unroll
-                for (int j = 0; j < kJMax; ++j) acc[i][j] = fmaf(p[i], wv[j], acc[i][j]);
+                for (int i = 0; i < 4; ++i) acc[i][j] = __ffma2_rn(p[i], w2, acc[i][j]);
+            }
         }
     }
     __syncthreads();
@@ -135,7 +138,7 @@ fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q
     for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < kJMax; ++j)
-            if (j < jw) F_s[(tq * 8 + i) * ld + tc + 16 * j] = acc[i][j];
+            if (j < jw) F_s[(tq * 8 + i) * ld + tc + 16 * j] = (i & 1) ? acc[i >> 1][j].y : acc[i >> 1][j].x;
     __syncthreads();
 
     if (COLUMNS) {
