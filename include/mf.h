@@ -271,7 +271,8 @@ MF_API int mf_loglike_batch(mf_handle *const *hs, int n_events, const float *con
                             float *const *out_lnL, void *stream);
 
 /* ------------------------------------------------------------------------
- * Surrogate network (the learned part of the method's online stage): a
+ * Surrogate network (no counterpart in the paper: a learned stand-in for the
+ * interpolants of Eq. rbfcoeff, with the RBF path as its fallback): a
  * fully connected network n_in -> hidden (x n_hidden) -> n_out with SiLU
  * activations, FP32 master weights, BF16 GEMM operands and FP32
  * accumulation, trained on the GPU by the library's own forward, backward
@@ -318,7 +319,10 @@ MF_API int mf_mlp_train(mf_mlp *m, const float *X, const float *T, int n,
 MF_API int mf_mlp_query(const mf_mlp *m, const char *key, double *value);
 
 /* ------------------------------------------------------------------------
- * Learned surrogate of a handle's interpolant (form MF_FORM_MLP).  A
+ * Learned surrogate of a handle's interpolant (form MF_FORM_MLP; not in the
+ * paper: it replaces only the Phi.W stage, the time interpolation, amplitudes
+ * and quadratic form of Eqs. SVD, projected_h_fd and logl_complete are the
+ * RBF path's).  A
  * network 4 -> hidden (x n_hidden) -> K' (K' = K rounded up to 8), SiLU,
  * maps the metric-eigenbasis point x = R (theta - centre) to the per-column
  * standardised interpolated columns (node_values order); it is trained on
