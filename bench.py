@@ -4,14 +4,15 @@
 One step = one mf_loglike call over a batch of Q synthetic sampler points
 (the whole online stage: rotation, RBF + tail, Phi.W contraction, SVD
 reconstruction at each detector delay, extrinsic combination).  Default
-workload: C1 (3 detectors x 4 modes, N = 1500 nodes, rank 20, M = 512,
-Q = 65536 per step).  The line reports the fastest arithmetic form whose lnL
-stays within |dlnL| <= 0.01 of the FP64 oracle on a sample, next to the plain
-FP32 form, the kernel's roofline fraction, an end-to-end number through the C
-ABI with host buffers, and the FP64 CPU oracle timed on this host.
+workload: the largest single-GPU configuration, C4 (one detector, 4 modes,
+N = 8000 nodes, rank 80, M = 2048, Q = 10^6 per step).  The line reports the
+fastest arithmetic form whose lnL stays within |dlnL| <= 0.01 of the FP64
+oracle on a sample, next to the plain FP32 form, the kernel's roofline
+fraction, an end-to-end number through the C ABI with host buffers, the
+learned surrogate (C4), and the FP64 CPU oracle timed on this host.
 
-  python bench.py [--gpus N --steps K --warmup W --config C1 --forms fp32,fp16_3term]
-  python bench.py --config C4 --forms fp32,fp16_3term,mlp   # + learned surrogate
+  python bench.py [--gpus N --steps K --warmup W --config C4 --forms fp32,fp16_3term]
+  python bench.py --config C1        # 3 detectors x 4 modes, N = 1500, Q = 65536
   python bench.py --config C3        # 100 events, one persistent launch + CUDA graph
   python bench.py --impl reference ...   # FP64 CPU oracle arm
 """
@@ -36,7 +37,33 @@ sys.path.insert(0, ROOT)
 
 METRIC = "lnL evals/s at |ΔlnL|≤0.01 vs FP64 oracle, chosen vs plain form; % roofline"
 TOL = 0.01
-FP32_SIMT_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # 152 SMs x 128 FMA/clk x 2 x max clock
+CPU_SUBSET = 8192          # fixed query subset the CPU oracle is timed on for C2 and C4
+TERMS = {"fp32": 1, "fp16": 1, "bf16": 1, "fp16_wsplit": 2, "bf16_wsplit": 2, "fp16_3term": 3,
+         "bf16_3term": 3}
+
+
+def fp32_simt_peak(sm_max_mhz=None):
+    """FP32 FMA peak of this device: SMs (read from the device) x 128 FP32
+    lanes x 2 flop x the maximum SM clock (sampled by nvidia-smi, else the
+    measured value, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = sm_max_mhz
+    if not mhz:
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                mhz = json.load(f).get("sm_max_mhz")
+        except Exception:
+            mhz = None
+    mhz = float(mhz or 2070.0)
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x 128 FP32 FMA/clk x 2 flop x {mhz:.0f} MHz (derived)"
+
+
+def workload_name(spec) -> str:
+    """The workload string both arms print (the driver compares them)."""
+    P = 5 if spec.tail_degree == 1 else (1 if spec.tail_degree == 0 else 0)
+    return (f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, N={spec.N}+{P} nodes, "
+            f"rank {spec.rank}, M={spec.M}, K={spec.K}, Q={spec.Q} per step per GPU")
 
 
 def _peaks():
@@ -146,11 +173,11 @@ def _traffic_from_profile(kernel_tag: str, src_files):
     return None
 
 
-def build_workload(cfg: str, rank: int):
+def build_workload(cfg: str, rank: int, Q: int = 0):
     import paper_2508_04172_gb300 as mf
     from workload import standin
     from workload.standin import make_event, make_queries, spec_for
-    spec = spec_for(cfg)
+    spec = spec_for(cfg, Q=Q) if Q else spec_for(cfg)
     ev = make_event(spec)
     m = mf.Interpolant.from_overlaps(ev.nodes, standin.node_overlaps(ev),
                                      standin.standin_sigma(ev, ev.nodes), spec.rank, spec.eps,
@@ -213,9 +240,12 @@ def time_e2e(m, form, h_th, h_ex, h_out, steps, warmup, dev):
     return ms, h_th.numel() * 4 + h_ex.numel() * 4, Q * 4
 
 
-def oracle_baseline(ev, th, ex, budget_s=10.0, cap=None):
+def oracle_baseline(ev, th, ex, budget_s=10.0, cap=None, om=None):
+    """The FP64 oracle timed on this host: all queries for the small
+    workloads, the first `cap` queries (a fixed subset) for the large ones,
+    within about budget_s of CPU time."""
     import oracle
-    om = oracle.Model.from_event(ev)
+    om = om if om is not None else oracle.Model.from_event(ev)
     n0 = min(1024, th.shape[0])
     t = time.perf_counter()
     om.loglike(th[:n0], ex[:n0])
@@ -309,8 +339,8 @@ def run_ours(args):
     flops = 2.0 * Q * (N + P) * K
     kms = res[chosen]["kernel_ms"]
     if chosen == "fp32":
-        roof = {"bound": "alu", "peak": round(FP32_SIMT_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-                "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (derived)"}
+        pk, psrc = fp32_simt_peak(ck.get("sm_max_mhz"))
+        roof = {"bound": "alu", "peak": round(pk, 1), "unit": "TFLOP/s", "peak_source": psrc}
         tag, srcs = "fp32_kernel", ["paper_2508_04172_gb300/csrc/mf_fp32.cu",
                                     "paper_2508_04172_gb300/csrc/mf_epilogue.cuh"]
     else:
@@ -323,6 +353,11 @@ def run_ours(args):
     roof.update(achieved=round(achieved, 2), frac=round(achieved / roof["peak"], 4),
                 traffic=_traffic_from_profile(f"{tag}@{spec.name}", srcs), kernel=tag,
                 algorithmic_flops_per_launch=flops, kernel_ms=round(kms, 4))
+    if TERMS.get(chosen, 1) > 1:
+        # the split forms issue TERMS products per algorithmic one: the tensor
+        # pipe's own utilisation is frac x TERMS (ceiling 1 / TERMS for frac)
+        roof["products_per_term"] = TERMS[chosen]
+        roof["executed_frac"] = round(TERMS[chosen] * achieved / roof["peak"], 4)
 
     line = {"metric": METRIC, "value": round(value, 1), "unit": "evals/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
@@ -331,9 +366,7 @@ def run_ours(args):
                       "fp16": "f16", "bf16": "bf16", "fp16_wsplit": "f16x2",
                       "bf16_wsplit": "bf16x2"}.get(chosen, chosen),
             "data": "synthetic (seeded closed-form stand-in overlaps)",
-            "config": {"workload": f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, "
-                                   f"N={spec.N}+{P} nodes, rank {spec.rank}, M={spec.M}, "
-                                   f"K={K}, Q={Q} per step per GPU",
+            "config": {"workload": workload_name(spec),
                        "form": chosen, "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roof,
@@ -365,18 +398,28 @@ def run_ours(args):
                                                  "n_checked")},
             "evals_per_s": round(Q * world / (r["ms_per_step"] / 1e3), 1),
             "ms_per_step": round(r["ms_per_step"], 4),
-            "speedup_vs_plain_fp32": (round(res[plain]["ms_per_step"] / r["ms_per_step"], 2)
-                                      if plain in res and "error" not in res[plain] else None),
-            "speedup_vs_chosen_form": round(ms / r["ms_per_step"], 2),
+            # the surrogate's error is the network's approximation error, bounded by its
+            # held-out gate (0.1 max / 0.01 median), not by the 0.01 bar of the RBF forms:
+            # its speed-up is quoted at gate accuracy and is not a same-accuracy speed-up
+            # unless its max |dlnL| against the oracle meets that bar
+            "meets_tol": bool(r["max_abs_dlnl"] <= TOL),
+            "accuracy_basis": ("within the 0.01 bar" if r["max_abs_dlnl"] <= TOL
+                               else "fails the 0.01 bar: speed-up at the held-out gate's accuracy only"),
+            "speedup_vs_plain_fp32_at_gate_accuracy": (
+                round(res[plain]["ms_per_step"] / r["ms_per_step"], 2)
+                if plain in res and "error" not in res[plain] else None),
+            "speedup_vs_chosen_form_at_gate_accuracy": round(ms / r["ms_per_step"], 2),
             "fallback_rate": r.get("fallback_rate"),
             "train_ms": round(sur["surrogate_train_ms"], 1),
             "label_ms": round(sur["surrogate_label_ms"], 1),
             "final_train_loss": sur["surrogate_loss"],
             "tensor_tflops": round(fl * Q / (r["kernel_ms"] / 1e3) / 1e12, 2),
             "flops_per_eval": fl}
-    # CPU FP64 oracle on this host (rank 0, N = 1 only)
+    # CPU FP64 oracle on this host (rank 0, N = 1 only): all queries of the
+    # small workloads, a fixed subset (the first 8192) of the large ones
     if rank == 0 and world == 1:
-        _, _, n, rate, cores = oracle_baseline(ev, th, ex, budget_s=args.cpu_budget)
+        cap = CPU_SUBSET if Q > 65536 else None
+        _, _, n, rate, cores = oracle_baseline(ev, th, ex, budget_s=args.cpu_budget, cap=cap, om=om)
         line["cpu_baseline"] = {"value": round(rate, 1), "unit": "evals/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": f"first {n} queries of the {spec.name} batch, FP64 C "
@@ -385,6 +428,34 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_kernels_only(args):
+    """Only the GPU launches of the given forms on the workload (no oracle, no
+    CPU leg, no L2 flush): a short, self-contained command for profilers.
+    Prints one line per form with the mean time per launch."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    spec, ev, m, th, ex = build_workload(args.config, 0, args.queries)
+    d_th = torch.from_numpy(th).to(dev)
+    d_ex = torch.from_numpy(ex).to(dev)
+    d_out = torch.empty(spec.Q, dtype=torch.float32, device=dev)
+    for f in [x.strip() for x in args.forms.split(",") if x.strip()]:
+        m.set_form(f)
+        for _ in range(args.warmup):
+            m.loglike(d_th, d_ex, out=d_out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            m.loglike(d_th, d_ex, out=d_out)
+        e1.record()
+        e1.synchronize()
+        rc, n_bad = m.sync_status()
+        print(json.dumps({"kernels_only": spec.name, "form": f, "ms_per_launch":
+                          round(e0.elapsed_time(e1) / args.steps, 4), "status": rc, "n_bad": n_bad}),
+              flush=True)
 
 
 def run_batch(args):
@@ -591,6 +662,8 @@ def run_reference(args):
     per = (time.perf_counter() - t) / n0
     budget = 150.0 / max(1, args.steps + args.warmup)        # whole run within a few minutes
     n = int(max(256, min(spec.Q, budget / max(per, 1e-9))))
+    if spec.Q > 65536:
+        n = min(n, CPU_SUBSET)       # the fixed subset of the large workloads
     for i in range(args.warmup):
         om.loglike(th[:n], ex[:n])
     ts = []
@@ -605,8 +678,8 @@ def run_reference(args):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded closed-form stand-in overlaps)",
-            "config": {"workload": ("C3 (event 0 of the 100-event batch) " if args.config == "C3" else "") + f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, "
-                                   f"N={spec.N} nodes, rank {spec.rank}, M={spec.M}, K={spec.K}",
+            "config": {"workload": (("C3 (event 0 of the 100-event batch) " if args.config == "C3" else "")
+                                    + workload_name(spec)),
                        "form": "fp64 CPU oracle", "parallelism": "host cores"},
             "cpu_baseline": {"value": round(v, 1), "unit": "evals/s", "cores": oracle.num_threads(),
                              "kind": "oracle",
@@ -622,25 +695,32 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="C1", choices=["C0", "C1", "C2", "C3", "C4"])
+    ap.add_argument("--config", default="C4", choices=["C0", "C1", "C2", "C3", "C4"])
     ap.add_argument("--forms", default=None,
-                    help="comma list; default all RBF forms (C4: fp32,fp16_3term,mlp)")
+                    help="comma list; default the plain and both 3-term forms (C4: + the surrogate, "
+                         "C1/C2: + the single-product and W-split forms)")
     ap.add_argument("--check", type=int, default=2048, help="queries checked against the oracle")
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--surrogate-steps", type=int, default=0,
                     help="training steps of the surrogate (0: library default, 20000)")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="only the GPU launches of --forms (no oracle, no JSON bench line): for profilers")
+    ap.add_argument("--queries", type=int, default=0,
+                    help="with --kernels-only: batch size (0: the workload's Q)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.forms is None:
-        args.forms = ("fp32,fp16_3term,mlp" if args.config == "C4"
+        args.forms = ("fp32,fp16_3term,bf16_3term,mlp" if args.config == "C4"
                       else "fp32,fp16_3term,bf16_3term,fp16_wsplit,fp16,bf16")
     if args.impl == "reference":
         run_reference(args)
     else:
         import paper_2508_04172_gb300 as mf
         mf.build()
-        if args.config == "C3":
+        if args.kernels_only:
+            run_kernels_only(args)
+        elif args.config == "C3":
             run_batch(args)
         else:
             run_ours(args)

@@ -2,12 +2,12 @@
  * mf.h -- C ABI of the GB300 meshfree log-likelihood library (libmf.so).
  *
  * The library evaluates the online stage of the meshfree likelihood
- * interpolation of Sec. II E for large batches of sampler points: rotate the
+ * interpolation of Sec. II D for large batches of sampler points: rotate the
  * intrinsic point into the metric eigenbasis, evaluate the Gaussian RBF
  * interpolants with their polynomial tail (Eq. rbfcoeff) for every SVD
  * coefficient of every mode/detector overlap series and for the mode cross
  * terms, rebuild each detector's overlap at its delay with a cubic spline
- * through 10 samples (Eq. SVD + Sec. II E), and combine them with the
+ * through 10 samples (Eq. SVD + Sec. II D), and combine them with the
  * extrinsic amplitudes into lnL (Eqs. logl_basic, projected_h_fd,
  * hplus_hcross_decomposed1/2, logl_complete).
  *
@@ -128,7 +128,7 @@ MF_API int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m,
  *   basis : host [n_det][n_modes][rank][M][2] FP64 (re, im).
  *   t0, dt: time of sample 0 and the sample spacing (seconds).
  * The series is evaluated at t = t_c + dt_k with a not-a-knot cubic spline
- * through the 10 samples j-4..j+5, j = floor((t - t0)/dt) (Sec. II E).
+ * through the 10 samples j-4..j+5, j = floor((t - t0)/dt) (Sec. II D).
  */
 MF_API int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, double dt);
 
@@ -143,7 +143,7 @@ MF_API int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, dou
 MF_API int mf_set_detectors(mf_handle *h, const double *det, double d_ref);
 
 /*
- * Sampler frame -> metric eigenbasis (Sec. II E, Delta-e coordinates):
+ * Sampler frame -> metric eigenbasis (Sec. II D, Delta-e coordinates):
  * x = R (theta - centre), R = rows of metric eigenvectors by ascending
  * eigenvalue, each row's largest-|.| entry positive.  metric: host [4][4]
  * symmetric positive definite, or NULL for R = I.  centre: host [4] or NULL
@@ -176,10 +176,12 @@ MF_API int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrins
 /*
  * mf_loglike without any device allocation in the call.  The paper has no
  * counterpart: this is a service for callers that cannot allocate device
- * memory while they run -- code inside a CUDA stream capture, callers that
- * give all device memory to their own fixed pool, real-time sampler loops.
+ * memory while they run -- callers that give all device memory to their own
+ * fixed pool at start-up, and real-time sampler loops that forbid
+ * allocation (and the synchronisation it can bring) once they run.
  * Same arguments and results as mf_loglike with the plain FP32 form (the
- * handle must be in MF_FORM_FP32, else MF_E_STATE).  When the columns need
+ * handle must be in MF_FORM_FP32, else MF_E_STATE; the handle's device must
+ * be the current device, else MF_E_STATE).  When the columns need
  * several passes, the partial sums live in one fixed array of
  * MF_NOALLOC_MAX_PARTIAL floats (16 MiB) inside the library, which every GPU
  * that loads the library keeps until the process exits:
@@ -187,8 +189,10 @@ MF_API int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrins
  *     mf_query "n_pass"); nothing is launched.
  *   - All calls on a device share the array; calls that overlap on the GPU
  *     (other streams, other handles) race and must be serialised by the caller.
- *   - The first call on each device looks up the array's device address;
- *     make it before any stream capture starts.
+ *   - The first call on each device looks up the array's device address and
+ *     caches it; make that first call before any stream capture starts.  The
+ *     cached address does not survive cudaDeviceReset: after a reset, do not
+ *     call this entry point on that device again in the same process.
  */
 #define MF_NOALLOC_MAX_PARTIAL 4194304
 MF_API int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const float *extrinsic, int Q,
@@ -196,7 +200,13 @@ MF_API int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const float 
 
 /*
  * Interpolated columns only (the Phi.W stage, Eq. rbfcoeff), in the
- * node_values column order: out [Q][K] device FP32.  Asynchronous.
+ * node_values column order: out [Q][K] device FP32, computed in the handle's
+ * current form (FP32 SIMT, or the tcgen05 kernel of a 16-bit form with its
+ * epilogue writing columns instead of lnL; the FP16 column scales are
+ * undone), or in MF_FORM_MLP the trained network's de-standardised
+ * outputs for every query (no radius fallback; these are exactly the
+ * columns the surrogate's fused lnL epilogue combines).  intrinsic as in
+ * mf_loglike.  Asynchronous on `stream`.
  */
 MF_API int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *out, void *stream);
 

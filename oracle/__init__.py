@@ -10,9 +10,9 @@ online stage is written out as loops in ``mforacle.c``.
 Paper map:
   * ``svd_compress``      -- Eq. (SVD): SVD of the node-by-time overlap matrix.
   * ``rbf_fit``           -- Eq. (rbfcoeff) with the side condition P^T a = 0.
-  * ``metric_rotation``   -- Sec. II E: Delta-e = displacement along the metric
+  * ``metric_rotation``   -- Sec. II D: Delta-e = displacement along the metric
                              eigenvectors, smallest eigenvalue first.
-  * ``Model.loglike``     -- Sec. II E online stage + Eq. (logl_complete).
+  * ``Model.loglike``     -- Sec. II D online stage + Eq. (logl_complete).
 """
 from __future__ import annotations
 
@@ -69,10 +69,12 @@ def lib():
             L.oracle_amplitudes.argtypes = ([ctypes.POINTER(_Model), ctypes.c_int]
                                             + [ctypes.c_double] * 4 + [dp, dp])
             L.oracle_loglike.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, fp, fp,
-                                         ctypes.c_int, dp, ctypes.c_int]
+                                         ctypes.c_int, dp, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_int)]
             L.oracle_loglike.restype = ctypes.c_int
             L.oracle_loglike_columns.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, fp,
-                                                 ctypes.c_int, dp, ctypes.c_int]
+                                                 ctypes.c_int, dp, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_int)]
             L.oracle_loglike_columns.restype = ctypes.c_int
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
@@ -94,7 +96,7 @@ def sylm(s: int, l: int, m: int, theta: float, phi: float) -> complex:
 
 def spline(y, x: float) -> float:
     """Not-a-knot cubic spline through y at abscissae 0..n-1, evaluated at x
-    (the online-stage time interpolation, Sec. II E)."""
+    (the online-stage time interpolation, Sec. II D)."""
     y = np.ascontiguousarray(y, dtype=np.float64)
     return lib().oracle_spline(len(y), _dp(y), float(x))
 
@@ -137,7 +139,7 @@ def rbf_fit(nodes: np.ndarray, F: np.ndarray, eps: float, tail_degree: int = 1):
 
 def metric_rotation(metric) -> np.ndarray:
     """Rows = eigenvectors of the metric, ascending eigenvalue (Delta-e_0 along
-    the smallest, Sec. II E); each row's largest-|.| entry made positive."""
+    the smallest, Sec. II D); each row's largest-|.| entry made positive."""
     if metric is None:
         return np.eye(4)
     w, V = np.linalg.eigh(np.asarray(metric, dtype=np.float64))
@@ -243,10 +245,12 @@ class Model:
         th = np.ascontiguousarray(intrinsic, dtype=np.float32)
         ex = np.ascontiguousarray(extrinsic, dtype=np.float32)
         out = np.empty(th.shape[0])
+        herm = ctypes.c_int(0)
         lib().oracle_loglike(ctypes.byref(self._c), th.shape[0],
                              th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
                              ex.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                             ex.shape[1], _dp(out), nthreads)
+                             ex.shape[1], _dp(out), nthreads, ctypes.byref(herm))
+        _check_hermitian(herm.value)
         return out
 
 
@@ -258,10 +262,20 @@ def loglike_columns(model: "Model", F, extrinsic, nthreads: int = 0):
     ex = np.ascontiguousarray(extrinsic, dtype=np.float32)
     assert F.shape == (ex.shape[0], model.K)
     out = np.empty(ex.shape[0])
+    herm = ctypes.c_int(0)
     lib().oracle_loglike_columns(ctypes.byref(model._c), ex.shape[0], _dp(F),
                                  ex.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
-                                 ex.shape[1], _dp(out), nthreads)
+                                 ex.shape[1], _dp(out), nthreads, ctypes.byref(herm))
+    _check_hermitian(herm.value)
     return out
+
+
+def _check_hermitian(n_herm: int):
+    """c^H Sigma c must be real for every query (Sigma Hermitian by Eq.
+    conjugation_symmetry); a failure means the packed cross terms were
+    unpacked wrongly."""
+    if n_herm:
+        raise AssertionError(f"oracle: Im(c^H Sigma c) above 1e-9 relative for {n_herm} queries")
 
 
 def num_threads() -> int:

@@ -2,13 +2,13 @@
  * FP64 CPU oracle for the meshfree log-likelihood (TEST INFRASTRUCTURE).
  *
  * Plain, slow, obviously-correct loops that follow the paper's online stage
- * step by step (Sec. II E).  Only the test-suite, the smoke check and the
+ * step by step (Sec. II D).  Only the test-suite, the smoke check and the
  * benchmark's CPU-baseline leg may load this file; the GPU library shares no
  * code with it.
  *
  *  - RBF interpolant with polynomial tail ........ Eq. (rbfcoeff)
  *  - SVD reconstruction of the overlap series .... Eq. (SVD)
- *  - cubic spline through ~10 samples ............ Sec. II E (online stage)
+ *  - cubic spline through ~10 samples ............ Sec. II D (online stage)
  *  - spin-weighted spherical harmonics ........... Eq. (h_spherical_harmonic_basis)
  *  - polarisations from negative-m modes ......... Eqs. (hplus_hcross_decomposed1/2)
  *  - frozen antenna patterns + detector delay .... Eq. (projected_h_fd)
@@ -190,12 +190,15 @@ static int col_sigma0(const oracle_model *m, int k) {
 
 /* lnL of one query from its interpolated columns f[K] (node_values order):
  * time interpolation, amplitudes and Eq. logl_complete.  Returns 0, or 1
- * when the spline stencil leaves the sampled time window (then *out = NaN). */
+ * when the spline stencil leaves the sampled time window (then *out = NaN),
+ * or 2 when c^H Sigma c is not real to 1e-9 relative (the cross terms were
+ * not unpacked into a Hermitian Sigma; *out is still written). */
 static int loglike_from_columns(const oracle_model *m, const double *f, const double *ext,
                                 double *out) {
     const int nm = m->n_modes, S = m->stencil, half = S / 2 - 1;
     double c_re[8], c_im[8], ys_re[32], ys_im[32];
     double lnl = 0.0;
+    int herm_bad = 0;
     for (int k = 0; k < m->n_det; ++k) {
         double t = (double)ext[4] + m->det[k * 3 + 2];
         double s = (t - m->t0) / m->dt;
@@ -239,25 +242,27 @@ static int loglike_from_columns(const oracle_model *m, const double *f, const do
                 q_re += c_re[a] * xr + c_im[a] * xi;
                 q_im += c_re[a] * xi - c_im[a] * xr;
             }
-        (void)q_im;
+        /* Sigma Hermitian => c^H Sigma c real (Eq. conjugation_symmetry) */
+        if (!(fabs(q_im) <= 1e-9 * fabs(q_re) + 1e-300)) herm_bad = 1;
         lnl -= 0.5 * q_re;
     }
     *out = lnl;
-    return 0;
+    return herm_bad ? 2 : 0;
 }
 
 /* lnL for Q queries; intrinsic [Q][4] (sampler frame), extrinsic [Q][E]
  * = (d_L, cos iota, psi, phi_c, t_c).  Inputs are the FP32 values the GPU
- * receives, promoted to FP64.  Returns the number of out-of-window queries. */
+ * receives, promoted to FP64.  Returns the number of out-of-window queries;
+ * *n_herm = queries whose c^H Sigma c had an imaginary part. */
 int oracle_loglike(const oracle_model *m, int Q, const float *intrinsic, const float *extrinsic,
-                   int E, double *out, int nthreads) {
-    int bad = 0;
+                   int E, double *out, int nthreads, int *n_herm) {
+    int bad = 0, herm = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
     (void)nthreads;
 #endif
-    #pragma omp parallel reduction(+:bad)
+    #pragma omp parallel reduction(+:bad, herm)
     {
         double *f = (double *)malloc(sizeof(double) * (size_t)m->K);
         #pragma omp for schedule(dynamic, 8)
@@ -268,30 +273,37 @@ int oracle_loglike(const oracle_model *m, int Q, const float *intrinsic, const f
             double x[4];
             rotate(m, th, x);
             rbf_eval_point(m, x, f);
-            bad += loglike_from_columns(m, f, ex, out + q);
+            const int st = loglike_from_columns(m, f, ex, out + q);
+            bad += st == 1;
+            herm += st == 2;
         }
         free(f);
     }
+    *n_herm = herm;
     return bad;
 }
 
 /* lnL for Q queries whose interpolated columns are given: F [Q][K] in the
  * node_values column order (e.g. a surrogate's prediction), extrinsic as in
- * oracle_loglike.  Returns the number of out-of-window queries. */
+ * oracle_loglike.  Returns the number of out-of-window queries; *n_herm as
+ * in oracle_loglike. */
 int oracle_loglike_columns(const oracle_model *m, int Q, const double *F, const float *extrinsic,
-                           int E, double *out, int nthreads) {
-    int bad = 0;
+                           int E, double *out, int nthreads, int *n_herm) {
+    int bad = 0, herm = 0;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
     (void)nthreads;
 #endif
-    #pragma omp parallel for reduction(+:bad) schedule(dynamic, 8)
+    #pragma omp parallel for reduction(+:bad, herm) schedule(dynamic, 8)
     for (int q = 0; q < Q; ++q) {
         double ex[5];
         for (int i = 0; i < 5; ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
-        bad += loglike_from_columns(m, F + (size_t)q * m->K, ex, out + q);
+        const int st = loglike_from_columns(m, F + (size_t)q * m->K, ex, out + q);
+        bad += st == 1;
+        herm += st == 2;
     }
+    *n_herm = herm;
     return bad;
 }
 

@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY: used by tests/ and the benchmark's CPU baseline to
 check the GPU kernels; nothing in the product path imports it.
 
 The surrogate maps the rotated intrinsic coordinates x (4 numbers, the same
-metric-eigenbasis point the RBF interpolant is evaluated at, Sec. II E) to
+metric-eigenbasis point the RBF interpolant is evaluated at, Sec. II D) to
 the interpolated columns F(x) (per-column standardised).  Network:
 
     h0 = x

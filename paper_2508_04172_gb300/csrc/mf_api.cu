@@ -461,8 +461,13 @@ int mf_eval_columns(mf_handle *h, const float *intrinsic, int Q, float *out, voi
     if (!intrinsic || !out) return MF_E_INVAL;
     if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;
     if (!h->have_layout) return MF_E_STATE;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (mf::is_tc_form(h->form))
+        return h->tc_tmem ? mf::launch_tc2(h, intrinsic, nullptr, Q, 5, nullptr, st, nullptr, out)
+                          : mf::launch_tc(h, intrinsic, nullptr, Q, 5, nullptr, st, nullptr, out);
+    if (h->form == MF_FORM_MLP) return mf::eval_columns_surrogate(h, intrinsic, Q, out, st);
     if (h->form != MF_FORM_FP32) return MF_E_NOTIMPL;
-    return mf::launch_fp32_columns(h, intrinsic, Q, out, (cudaStream_t)stream);
+    return mf::launch_fp32_columns(h, intrinsic, Q, out, st);
 }
 
 int mf_set_option(mf_handle *h, const char *key, double value) {

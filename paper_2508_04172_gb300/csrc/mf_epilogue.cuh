@@ -207,4 +207,25 @@ __device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, co
     return lnl;
 }
 
+// Interpolated columns of one pass for one query: the Phi.W stage alone
+// (Eq. rbfcoeff), scattered into the query's row of out [Q][K] in the
+// node_values column order; padding columns (user column -1) are dropped.
+// The loop is warp-uniform (the tcgen05 accessor loads are warp-collective);
+// row == nullptr (a query past the batch) loads without storing.
+template <class Acc>
+__device__ __forceinline__ void pass_columns(const Pass &ps, Acc &acc, const int *__restrict__ user_of_dev,
+                                             float *row) {
+    for (int c = 0; c < ps.width; c += 8) {
+        float f[8];
+        acc.load8(c, f);
+        if (row) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int u = __ldg(user_of_dev + ps.col0 + c + e);
+                if (u >= 0) row[u] = f[e];
+            }
+        }
+    }
+}
+
 }  // namespace mf

@@ -1,7 +1,7 @@
 // Plain FP32 form of the fused lnL kernel (SIMT FMAs, no tensor cores).
 //
 // One CTA evaluates one (query tile of 128, column pass) work item:
-//   1. rotate the 128 queries into the metric eigenbasis (Sec. II E, Delta-e),
+//   1. rotate the 128 queries into the metric eigenbasis (Sec. II D, Delta-e),
 //   2. per chunk of 32 interpolation nodes: Gaussian RBF values (or the tail
 //      monomials 1, x1..x4 for the last P rows) into shared memory, the weight
 //      chunk into shared memory, and an 8x12 register-tiled FMA update of the

@@ -178,12 +178,13 @@ RotParams make_rot(const mf_handle *h);
 int launch_fp32(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
                 cudaStream_t st, float *partial);
 int launch_fp32_columns(mf_handle *h, const float *intr, int Q, float *out, cudaStream_t st);
+// cols != nullptr: interpolated columns only, out [Q][K] (mf_eval_columns)
 int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-              cudaStream_t st, float *partial);
+              cudaStream_t st, float *partial, float *cols = nullptr);
 int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStream_t st,
                    unsigned long long *bad);
 int launch_tc2(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-               cudaStream_t st, float *partial);
+               cudaStream_t st, float *partial, float *cols = nullptr);
 int tc2_pass_max();
 // batched tcgen05 launch (all events share form and mode count)
 int fill_tc_event(const mf_handle *h, TcEvent *out);
@@ -198,6 +199,7 @@ void free_surrogate(mf_handle *h);
 int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
                       cudaStream_t st, bool force_net);
 int surrogate_query(const mf_handle *h, const std::string &key, double *value);
+int eval_columns_surrogate(mf_handle *h, const float *intr, int Q, float *out, cudaStream_t st);
 // tensor map of a 16-bit [rows][K] matrix (at: 0 = FP16, 1 = BF16), box K 32 x box_rows
 int make_tmap(void *out, void *base, int at, int K, int rows, int box_rows);
 }  // namespace mf

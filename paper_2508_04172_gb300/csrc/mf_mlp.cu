@@ -567,6 +567,8 @@ struct mf_surrogate {
     float *d_ci = nullptr, *d_ce = nullptr, *d_co = nullptr, *d_cpart = nullptr;   // compacted copies
     double fallback_rate = 0;
     int last_launches = 0;                        // kernels launched by the last mf_loglike
+    float *d_colbuf = nullptr;                    // [chunk][Kdev] network columns (mf_eval_columns)
+    size_t colbuf_cap = 0;
 };
 
 namespace mf {
@@ -743,6 +745,17 @@ __global__ void sur_scatter_kernel(const int *__restrict__ list, const int *__re
     if (j < *count) out[list[j]] = v[j];
 }
 
+// Network columns in the device layout -> node_values order (one thread per
+// (query, device column); padding columns are dropped).
+__global__ void sur_gather_cols(const float *__restrict__ dev, int Qc, int Kdev, const int *__restrict__ user_of_dev,
+                                int K, float *__restrict__ out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)Qc * Kdev) return;
+    const int q = (int)(i / (size_t)Kdev), c = (int)(i % (size_t)Kdev);
+    const int u = user_of_dev[c];
+    if (u >= 0) out[(size_t)q * K + u] = dev[i];
+}
+
 void free_infer(mf_surrogate *s) {
     auto fr = [](void *p) { if (p) cudaFree(p); };
     fr(s->d_h[0]); fr(s->d_h[1]); fr(s->d_part);
@@ -760,7 +773,7 @@ void destroy_surrogate(mf_surrogate *s) {
     free_infer(s);
     if (s->net) destroy_mlp(s->net);
     auto fr = [](void *p) { if (p) cudaFree(p); };
-    fr(s->d_mu); fr(s->d_s); fr(s->d_Wdev); fr(s->d_bdev);
+    fr(s->d_mu); fr(s->d_s); fr(s->d_Wdev); fr(s->d_bdev); fr(s->d_colbuf);
     delete s;
 }
 
@@ -827,6 +840,64 @@ int surrogate_prepare(mf_handle *h) {
 void free_surrogate(mf_handle *h) {
     destroy_surrogate(h->sur);
     h->sur = nullptr;
+}
+
+// The network's interpolated columns (node_values order) for Q queries:
+// the same input layer and hidden GEMMs as the lnL path, the final layer
+// stored in FP32 (the accumulators the fused lnL epilogue reads) and
+// gathered into the user column order.  Every query goes through the
+// network, whatever its radius or the gate.
+int eval_columns_surrogate(mf_handle *h, const float *intr, int Q, float *out, cudaStream_t st) {
+    mf_surrogate *s = h->sur;
+    if (!s || !s->net || !s->d_Wdev) return MF_E_STATE;
+    mf_mlp *m = s->net;
+    const int H = m->H;
+    const int np = (int)h->passes.size();
+    const int chunk = std::min(Q, 1 << 14);
+    int rc = ensure_infer(s, chunk, Q, 5, np);
+    if (rc) return rc;
+    const size_t need = (size_t)chunk * h->Kdev;
+    if (need > s->colbuf_cap) {
+        if (s->d_colbuf) cudaFree(s->d_colbuf);
+        s->d_colbuf = nullptr;
+        s->colbuf_cap = 0;
+        MF_CUDA(cudaMalloc((void **)&s->d_colbuf, 4 * need));
+        s->colbuf_cap = need;
+    }
+    const RotParams rot = make_rot(h);
+    for (int q0 = 0; q0 < Q; q0 += chunk) {
+        const int Qc = std::min(chunk, Q - q0);
+        sur_input_kernel<<<(unsigned)((Qc + 127) / 128), 128, 0, st>>>(
+            intr + (size_t)q0 * 4, Qc, rot, m->d_p, m->d_p + H * 4, H, s->d_h[0], 1e30f, s->d_flag + q0,
+            s->d_count);
+        MF_CUDA(cudaGetLastError());
+        int cur = 0;
+        for (int l = 1; l < m->L - 1; ++l) {
+            GemmArgs g{};
+            g.bias = m->d_p + m->off[l] + H * H;
+            g.out_bf = s->d_h[cur ^ 1];
+            GemmPlan pl;
+            rc = make_plan(pl, EPI_SILU, s->d_h[cur], Qc, H, m->W[l], H, nt_hidden(H), g, h->d_err);
+            if (rc) return rc;
+            rc = launch_plan(pl, st);
+            if (rc) return rc;
+            cur ^= 1;
+        }
+        GemmArgs g{};
+        g.bias = s->d_bdev;
+        g.out_f = s->d_colbuf;
+        GemmPlan pl;
+        rc = make_plan(pl, EPI_F32, s->d_h[cur], Qc, H, s->d_Wdev, h->Kdev, nt_for(std::min(h->Kdev, 128)), g,
+                       h->d_err);
+        if (rc) return rc;
+        rc = launch_plan(pl, st);
+        if (rc) return rc;
+        const size_t n = (size_t)Qc * h->Kdev;
+        sur_gather_cols<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->d_colbuf, Qc, h->Kdev, h->d_user_of_dev,
+                                                                      h->K, out + (size_t)q0 * h->K);
+        MF_CUDA(cudaGetLastError());
+    }
+    return MF_OK;
 }
 
 // lnL through the network: chunks of queries through the hidden layers,

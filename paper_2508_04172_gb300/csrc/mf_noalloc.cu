@@ -1,14 +1,14 @@
 // mf_loglike_noalloc: the plain FP32 lnL path for callers that must not
 // allocate device memory during a call.
 //
-// Some callers cannot call cudaMalloc on their hot path: code running inside
-// a CUDA stream capture (allocation is not a capturable operation), callers
-// that hand all device memory to a fixed-size pool of their own, and
-// real-time sampler loops that forbid any allocation after start-up.  When a
-// handle's columns are split into several passes, mf_loglike needs a scratch
-// buffer of n_pass * Q partial sums and grows one with cudaMalloc on demand.
-// This entry point keeps that scratch in a fixed-size array in the library's
-// own device memory instead, so the call itself allocates nothing.
+// Some callers cannot call cudaMalloc on their hot path: callers that hand
+// all device memory to a fixed-size pool of their own at start-up, and
+// real-time sampler loops that forbid any allocation (and the implicit
+// device synchronisation cudaMalloc/cudaFree may bring) once they run.  When
+// a handle's columns are split into several passes, mf_loglike needs a
+// scratch buffer of n_pass * Q partial sums and grows one with cudaMalloc on
+// demand.  This entry point keeps that scratch in a fixed-size array in the
+// library's own device memory instead, so the call itself allocates nothing.
 //
 // The array (kNoallocMaxPartial floats, 16 MiB) is a file-scope __device__
 // variable: every GPU that loads the library holds it until the process exits,
@@ -20,7 +20,9 @@
 // Host code cannot use `g_noalloc_partial` as a device pointer (in host code
 // the name is a host-side shadow).  The first call on each device looks up the
 // device address with cudaGetSymbolAddress, with that device current, and
-// caches it; make that first call before any stream capture begins.
+// caches it.  The cache belongs to the device's primary context: after a
+// cudaDeviceReset in this process the cached address is stale, so a process
+// that resets a device must not call this entry point on it again.
 #include "mf_internal.cuh"
 
 #include <mutex>
@@ -65,6 +67,10 @@ extern "C" int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const fl
     if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;   // rows are read as float4
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
     if (h->form != MF_FORM_FP32 || !h->d_W32) return MF_E_STATE;
+    // the handle's buffers and the scratch address belong to h->dev
+    int cur = -1;
+    MF_CUDA(cudaGetDevice(&cur));
+    if (cur != h->dev) return MF_E_STATE;
     const size_t np = h->passes.size();
     if (np > 1 && np * (size_t)Q > kNoallocMaxPartial) {
         mf::log_msg("noalloc: n_pass * Q = %zu exceeds the %zu-float scratch", np * (size_t)Q,

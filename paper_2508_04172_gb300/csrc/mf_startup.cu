@@ -6,7 +6,7 @@
 //   * SVD compression of an overlap matrix, Eq. (SVD): dense FP64 SVD of the
 //     node-by-time matrix, projection C = Z V.
 //   * 4x4 metric eigendecomposition (cyclic Jacobi) for the Delta-e rotation
-//     (Sec. II E) and the 10-sample not-a-knot spline operator (Sec. II E).
+//     (Sec. II D) and the 10-sample not-a-knot spline operator (Sec. II D).
 // Dense factorizations use cuSOLVER and the Gram/projection GEMMs cuBLAS; the
 // matrix assembly, Schur step, iterations and small solves are kernels here.
 #include "mf_internal.cuh"

@@ -44,6 +44,9 @@ struct TcCall {
     int sb;                 // W ring depth
     int nbox_max;           // W ring slot rows
     unsigned *err;          // device status words
+    float *cols;            // columns-only launch: out [Q][K] (node_values order)
+    const int *umap;        // columns-only launch: device column -> user column
+    int K;                  // columns-only launch: row stride of cols
 };
 
 // Work source of the single-event kernel: work item = query tile.
@@ -155,9 +158,14 @@ __device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, in
 // every barrier is waited on phase by phase by its waiters.  Every mbarrier
 // wait is bounded and sets a status bit instead of hanging.  Every event of
 // a batch has exactly np passes.
-template <int NM, int AT, int TERMS, class Src>
+//
+// COLS = true is the columns-only variant (mf_eval_columns): the epilogue
+// writes the pass's interpolated columns of each query to cols [Q][K] (user
+// column order via umap) instead of combining them into lnL.
+template <int NM, int AT, int TERMS, class Src, bool COLS = false>
 __device__ __forceinline__ void tc_body(const Src &src, const int np, const int nbox_max, const int SB,
-                                        const int nc, const int E, unsigned *err) {
+                                        const int nc, const int E, unsigned *err, float *cols = nullptr,
+                                        const int *umap = nullptr, int K = 0) {
     constexpr int NA = (TERMS == 3) ? 2 : 1;
     constexpr int NB = (TERMS >= 2) ? 2 : 1;
     constexpr int SP = kSlotsPerProducer;
@@ -461,7 +469,8 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
             const int acc = i & 1;
             const int q = tile * kTile + row;
             const int qc = min(q, io.Q - 1);
-            QueryExt x = load_ext(ev.epi, io.ext, E, qc);
+            QueryExt x{};
+            if (!COLS) x = load_ext(ev.epi, io.ext, E, qc);
             bool ok = mbar_wait(tfull + acc, ((uint32_t)i >> 1) & 1, err, 7, i);
             ok = __all_sync(0xffffffffu, ok);    // tcgen05.ld below is warp-collective
             tc_fence_after();
@@ -469,14 +478,18 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
             if (ok) {
                 TmemAcc<false> tacc{tmem + (uint32_t)(acc * kAccCols) + ((uint32_t)(quad * 32) << 16),
                              ev.colscale ? ev.colscale + ps.col0 : nullptr};
-                bool bad = false;
-                l = pass_lnl<NM>(ev.epi, ps, x, tacc, bad);
-                if (bad) l = __int_as_float(0x7fc00000);
+                if (COLS) {
+                    pass_columns(ps, tacc, umap, q < io.Q ? cols + (size_t)q * K : nullptr);
+                } else {
+                    bool bad = false;
+                    l = pass_lnl<NM>(ev.epi, ps, x, tacc, bad);
+                    if (bad) l = __int_as_float(0x7fc00000);
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + acc);
-            if (q < io.Q) {
+            if (!COLS && q < io.Q) {
                 if (np == 1) {
                     io.out[q] = l;
                     if (l != l) atomicAdd(ev.epi.bad, 1ull);
@@ -496,11 +509,12 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
     }
 }
 
-template <int NM, int AT, int TERMS>
+template <int NM, int AT, int TERMS, bool COLS = false>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ TcCall call) {
     SingleSrc src{&ev, &call};
-    tc_body<NM, AT, TERMS>(src, ev.epi.n_pass, call.nbox_max, call.sb, call.n_clusters, call.E, call.err);
+    tc_body<NM, AT, TERMS, SingleSrc, COLS>(src, ev.epi.n_pass, call.nbox_max, call.sb, call.n_clusters, call.E,
+                                           call.err, call.cols, call.umap, call.K);
 }
 
 template <int NM, int AT, int TERMS>
@@ -590,6 +604,15 @@ void *pick2(int terms, bool batch) {
 template <int NM>
 void *pick1(int at, int terms, bool batch) {
     return at == 0 ? pick2<NM, 0>(terms, batch) : pick2<NM, 1>(terms, batch);
+}
+// Columns-only kernels do not depend on the mode count (no lnL epilogue).
+void *pick_cols_kernel(mf_form f) {
+    const int at = form_type(f), terms = form_terms(f);
+    if (at == 0)
+        return terms == 1 ? (void *)tc_kernel<1, 0, 1, true> : terms == 2 ? (void *)tc_kernel<1, 0, 2, true>
+                                                                          : (void *)tc_kernel<1, 0, 3, true>;
+    return terms == 1 ? (void *)tc_kernel<1, 1, 1, true> : terms == 2 ? (void *)tc_kernel<1, 1, 2, true>
+                                                                      : (void *)tc_kernel<1, 1, 3, true>;
 }
 void *pick_kernel(mf_form f, int n_modes, bool batch) {
     const int at = form_type(f), terms = form_terms(f);
@@ -746,17 +769,22 @@ int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBat
     return MF_OK;
 }
 
+// cols != nullptr: the columns-only variant, out [Q][K] (ext, out, partial unused).
 int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-              cudaStream_t st, float *partial) {
+              cudaStream_t st, float *partial, float *cols) {
     if (!h->d_Whi) return MF_E_STATE;
     const int np = (int)h->passes.size();
     if (np > kMaxCluster) return MF_E_NOTIMPL;
-    void *kern = pick_kernel(h->form, h->n_modes, false);
+    void *kern = cols ? pick_cols_kernel(h->form) : pick_kernel(h->form, h->n_modes, false);
     if (!kern) return MF_E_NOTIMPL;
     TcEvent ev;
     int rc = fill_tc_event(h, &ev);
     if (rc) return rc;
     TcCall c;
+    memset(&c, 0, sizeof(c));
+    c.cols = cols;
+    c.umap = h->d_user_of_dev;
+    c.K = h->K;
     c.intr = intr;
     c.ext = ext;
     c.out = out;

@@ -70,9 +70,14 @@ struct Tc2Call {
     int sa;                // A ring depth (TMEM stages)
     int nbox;              // W tile rows (widest pass)
     unsigned *err;
+    float *cols;           // columns-only launch: out [Q][K] (node_values order)
+    const int *umap;       // columns-only launch: device column -> user column
+    int K;
 };
 
-template <int NM, int AT, int TERMS>
+// COLS = true: columns-only variant (mf_eval_columns), the epilogue writes
+// each pass's interpolated columns instead of combining them into lnL.
+template <int NM, int AT, int TERMS, bool COLS = false>
 __global__ void __launch_bounds__(kThreads2, 1)
 tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c) {
     constexpr int NA = (TERMS == 3) ? 2 : 1;      // A parts in TMEM
@@ -298,7 +303,8 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
             const int acc = i & 1;
             const int q = tile * kTile + r;
             const int qc = min(q, c.Q - 1);
-            QueryExt x = load_ext(ev.epi, c.ext, c.E, qc);
+            QueryExt x{};
+            if (!COLS) x = load_ext(ev.epi, c.ext, c.E, qc);
             bool ok = mbar_wait(tfull + acc, ((uint32_t)i >> 1) & 1, err, 7, i);
             ok = __all_sync(0xffffffffu, ok);
             tc_fence_after();
@@ -306,14 +312,18 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
             if (ok) {
                 TmemAcc<false> tacc{tmem + (uint32_t)(acc * kAcc2) + ((uint32_t)(quad * 32) << 16),
                                     ev.colscale ? ev.colscale + ps.col0 : nullptr, nullptr};
-                bool bad = false;
-                l = pass_lnl<NM>(ev.epi, ps, x, tacc, bad);
-                if (bad) l = __int_as_float(0x7fc00000);
+                if (COLS) {
+                    pass_columns(ps, tacc, c.umap, q < c.Q ? c.cols + (size_t)q * c.K : nullptr);
+                } else {
+                    bool bad = false;
+                    l = pass_lnl<NM>(ev.epi, ps, x, tacc, bad);
+                    if (bad) l = __int_as_float(0x7fc00000);
+                }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty + acc);
-            if (q < c.Q) {
+            if (!COLS && q < c.Q) {
                 if (c.n_pass == 1) {
                     c.out[q] = l;
                     if (l != l) atomicAdd(ev.epi.bad, 1ull);
@@ -359,13 +369,20 @@ int form_terms_of(mf_form f) {
 int tc2_pass_max() { return kAcc2; }
 
 int launch_tc2(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out, cudaStream_t st,
-               float *partial) {
+               float *partial, float *cols) {
     if (!h->d_Whi) return MF_E_STATE;
     if (h->nbox > kAcc2) return MF_E_NOTIMPL;
     const int at = (h->form == MF_FORM_BF16 || h->form == MF_FORM_BF16_WSPLIT || h->form == MF_FORM_BF16_3TERM) ? 1 : 0;
     const int terms = form_terms_of(h->form);
     void *kern = nullptr;
-    switch (h->n_modes) {
+    if (cols) {   // columns only: independent of the mode count
+        if (at == 0)
+            kern = terms == 1 ? (void *)tc2_kernel<1, 0, 1, true> : terms == 2 ? (void *)tc2_kernel<1, 0, 2, true>
+                                                                              : (void *)tc2_kernel<1, 0, 3, true>;
+        else
+            kern = terms == 1 ? (void *)tc2_kernel<1, 1, 1, true> : terms == 2 ? (void *)tc2_kernel<1, 1, 2, true>
+                                                                              : (void *)tc2_kernel<1, 1, 3, true>;
+    } else switch (h->n_modes) {
         case 1: kern = pick_n<1>(at, terms); break;
         case 2: kern = pick_n<2>(at, terms); break;
         case 3: kern = pick_n<3>(at, terms); break;
@@ -389,6 +406,9 @@ int launch_tc2(mf_handle *h, const float *intr, const float *ext, int Q, int E, 
     c.n_items = c.n_tiles * c.n_pass;
     c.nbox = h->nbox;
     c.err = h->d_err;
+    c.cols = cols;
+    c.umap = h->d_user_of_dev;
+    c.K = h->K;
     const int NA = terms == 3 ? 2 : 1;
     c.sa = std::min(kMaxStages2, (512 - kARing0) / (NA * kACols));
     c.sb = h->tc_nbs ? h->tc_nbs : kMaxStages2;

@@ -8,9 +8,10 @@ from tests import _cases
 
 pytestmark = pytest.mark.gpu
 
-# per-form bounds on max |dlnL|: the chosen forms must
-# meet the 0.01 bar; the others are run and bounded loosely.
-BOUND = {"fp32": 0.01, "fp16_3term": 0.01, "bf16_3term": 0.03,
+# per-form bounds on max |dlnL|: the forms the benchmark may choose (plain
+# FP32 and both 3-term forms) must meet the 0.01 bar; the others are run and
+# bounded loosely.
+BOUND = {"fp32": 0.01, "fp16_3term": 0.01, "bf16_3term": 0.01,
          "fp16_wsplit": 5.0, "fp16": 5.0, "bf16_wsplit": 50.0, "bf16": 50.0}
 
 

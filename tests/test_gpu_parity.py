@@ -112,16 +112,18 @@ TOL_CHOSEN = 0.01
 # Expected accuracy of the other forms on C1 (probe of the arithmetic): the
 # plain 16-bit and weight-split forms lose to the cancellation in the RBF
 # weights (sum |a_n phi_n| / |F| ~ 1e5); they run, but are not chosen.
-LOOSE = {"bf16_3term": 0.2, "fp16_wsplit": 50.0, "bf16_wsplit": 500.0, "fp16": 50.0,
-         "bf16": 500.0}
+LOOSE = {"fp16_wsplit": 50.0, "bf16_wsplit": 500.0, "fp16": 50.0, "bf16": 500.0}
 
 
-@pytest.mark.parametrize("cfg,Q", [("C0", 1031), ("C1", 1500)])
-def test_tc_fp16_3term_parity(cfg, Q):
-    th, ex = _cases.queries(cfg, Q, seed=9)
+@pytest.mark.parametrize("form", ["fp16_3term", "bf16_3term"])
+@pytest.mark.parametrize("cfg,Q", [("C0", 1031), ("C1", 1500), ("C1", 2000)])
+def test_tc_3term_parity(cfg, Q, form):
+    """The 3-term forms are the ones the benchmark may choose: both are held
+    to the 0.01 bar on several tiles with a ragged last tile."""
+    th, ex = _cases.queries(cfg, Q, seed=9 if Q != 2000 else 12)
     ref = _cases.oracle_model(cfg).loglike(th, ex)
     m = _cases.gpu_model(cfg)
-    m.set_form("fp16_3term")
+    m.set_form(form)
     try:
         got = _run(m, th, ex)
         assert m.sync_status()[0] == 0
@@ -129,7 +131,7 @@ def test_tc_fp16_3term_parity(cfg, Q):
         m.set_form("fp32")
     err = np.abs(got - ref)
     assert np.all(np.isfinite(got))
-    assert err.max() <= TOL_CHOSEN, (err.max(), np.median(err))
+    assert err.max() <= TOL_CHOSEN, (form, err.max(), np.median(err))
 
 
 @pytest.mark.parametrize("form", sorted(LOOSE))

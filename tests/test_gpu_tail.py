@@ -1,0 +1,44 @@
+"""Polynomial tail degrees other than 1 (Eq. rbfcoeff with tail_degree 0:
+a constant, and -1: no tail) on the GPU against the FP64 oracle built with
+the same degree, in the plain FP32 form and a tcgen05 3-term form."""
+import numpy as np
+import pytest
+
+from tests import _cases
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(model, th, ex):
+    import torch
+    out = model.loglike(torch.from_numpy(th).cuda(), torch.from_numpy(ex).cuda())
+    torch.cuda.synchronize()
+    return out.cpu().numpy().astype(np.float64)
+
+
+@pytest.mark.parametrize("form", ["fp32", "fp16_3term"])
+@pytest.mark.parametrize("cfg", ["C0", "C1"])
+@pytest.mark.parametrize("tail", [0, -1])
+def test_tail_degree_parity(cfg, tail, form):
+    th, ex = _cases.queries(cfg, 1100, seed=31, tail_degree=tail)
+    ref = _cases.oracle_model(cfg, tail_degree=tail).loglike(th, ex)
+    m = _cases.gpu_model(cfg, tail_degree=tail)
+    m.set_form(form)
+    try:
+        got = _run(m, th, ex)
+        assert m.sync_status()[0] == 0
+    finally:
+        m.set_form("fp32")
+    assert np.all(np.isfinite(got))
+    err = np.abs(got - ref)
+    assert err.max() <= 0.01, (cfg, tail, form, err.max())
+
+
+def test_tail_degree_changes_the_fit():
+    """The three degrees are different interpolants (the tail enters the
+    solve): their lnL differ by far more than the rounding bar off the nodes."""
+    th, ex = _cases.queries("C0", 256, seed=32)
+    a = _run(_cases.gpu_model("C0", tail_degree=1), th, ex)
+    b = _run(_cases.gpu_model("C0", tail_degree=0), th, ex)
+    c = _run(_cases.gpu_model("C0", tail_degree=-1), th, ex)
+    assert np.abs(a - b).max() > 0.03 and np.abs(a - c).max() > 0.03

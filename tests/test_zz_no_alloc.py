@@ -1,9 +1,11 @@
 """mf_loglike_noalloc, the entry point for callers that cannot allocate device
-memory during a call (stream capture, fixed memory pools, real-time loops).
+memory during a call (fixed memory pools handed out at start-up, real-time
+sampler loops that forbid allocation once they run).
 
-It must return the same lnL as mf_loglike (plain FP32 form) on consecutive
-calls that share its fixed scratch array, and refuse batches whose partial
-sums would not fit.  This file is collected last on purpose."""
+It runs the same kernels as mf_loglike (plain FP32 form) in the same order,
+so on consecutive calls that share its fixed scratch array it must return
+bit-identical lnL; it must refuse batches whose partial sums would not fit.
+This file is collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -42,6 +44,7 @@ def test_noalloc_matches_loglike_on_two_calls():
         b = ref.cpu().numpy().astype(np.float64)
         assert np.all(np.isfinite(a))
         assert np.abs(a - b).max() <= TOL_FP32
+        assert np.array_equal(a, b)        # same kernels, same order: bit-identical
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch():
