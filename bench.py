@@ -182,7 +182,7 @@ def build_workload(cfg: str, rank: int, Q: int = 0):
     m = mf.Interpolant.from_overlaps(ev.nodes, standin.node_overlaps(ev),
                                      standin.standin_sigma(ev, ev.nodes), spec.rank, spec.eps,
                                      spec.modes, ev.det, spec.t0, spec.dt, spec.d_ref, ev.metric,
-                                     ev.centre, spec.tail_degree, "fp32")
+                                     ev.centre, spec.tail_degree, "fp32", sky=ev.sky)
     th, ex = make_queries(ev, spec.Q, seed=_rank_seed(spec.seed, rank))
     return spec, ev, m, th, ex
 
@@ -695,7 +695,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="C4", choices=["C0", "C1", "C2", "C3", "C4"])
+    ap.add_argument("--config", default="C4", choices=["C0", "C1", "C2", "C3", "C4", "C1S", "C4S", "C4T"])
     ap.add_argument("--forms", default=None,
                     help="comma list; default the plain and both 3-term forms (C4: + the surrogate, "
                          "C1/C2: + the single-product and W-split forms)")

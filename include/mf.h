@@ -143,6 +143,34 @@ MF_API int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, dou
 MF_API int mf_set_detectors(mf_handle *h, const double *det, double d_ref);
 
 /*
+ * Sky-dependent antenna patterns and delays (Eq. projected_h_td, long-
+ * wavelength response), in place of mf_set_detectors: mf_loglike then needs
+ * E >= 7 extrinsic columns, the last two being the source's right ascension
+ * alpha and declination delta (rad).  For channel k (a detector, or one
+ * frequency band of a detector whose signal lasts long enough for the Earth
+ * to turn: Sec. II B, 3G detectors) at the epoch t_c + tau_k:
+ *   hour angle h = gmst0 + omega (t_c + tau_k) - alpha,
+ *   source direction w = (cos delta cos h, -cos delta sin h, sin delta),
+ *   wave-frame axes X = cos psi X0 + sin psi Y0, Y = -sin psi X0 + cos psi Y0
+ *   with X0 = (-sin h, -cos h, 0), Y0 = (-cos h sin delta, sin h sin delta,
+ *   cos delta),
+ *   F+ = D : (X X - Y Y), Fx = D : (X Y + Y X), delay dt_k = -(r_k . w).
+ *   tensor : host [n_det][3][3] FP64 detector tensors D_k (symmetric; for
+ *            arms u, v: (u u^T - v v^T) / 2), Earth-fixed frame.
+ *   pos    : host [n_det][3] detector positions divided by c (seconds,
+ *            |.| <= 1), Earth-fixed frame.
+ *   tau    : host [n_det] epoch offsets (seconds, |.| <= 1e7), or NULL (0).
+ *   gmst0  : Greenwich sidereal angle (rad) at t_c = 0; omega: the Earth's
+ *            rotation rate (rad/s).  d_ref as in mf_set_detectors.
+ * The delay enters the spline time t_c + dt_k (Sec. II D), so every channel's
+ * basis must cover t_c + dt_k +- 5 samples (else NaN and MF_E_RANGE).
+ * MF_E_STATE before mf_set_layout; MF_E_INVAL for non-finite or out-of-range
+ * values.  mf_set_detectors switches back to frozen patterns.
+ */
+MF_API int mf_set_sky(mf_handle *h, const double *tensor, const double *pos, const double *tau,
+                      double gmst0, double omega, double d_ref);
+
+/*
  * Sampler frame -> metric eigenbasis (Sec. II D, Delta-e coordinates):
  * x = R (theta - centre), R = rows of metric eigenvectors by ascending
  * eigenvalue, each row's largest-|.| entry positive.  metric: host [4][4]
@@ -165,7 +193,8 @@ MF_API int mf_set_form(mf_handle *h, mf_form form);
  * intrinsic : device [Q][4] FP32, sampler-frame coordinates; 16-byte aligned
  *             (rows are read as float4), else MF_E_INVAL.
  * extrinsic : device [Q][E] FP32, E >= 5, columns (d_L [Mpc], cos iota,
- *             psi, phi_c, t_c [s]).
+ *             psi, phi_c, t_c [s]); after mf_set_sky E >= 7 and columns 5, 6
+ *             are (alpha, delta) [rad].
  * out_lnL   : device [Q] FP32, written by the call.
  * Queries whose spline stencil leaves the sampled window get NaN and are
  * counted; mf_sync_status() reports them.  Q == 0 is a no-op.  Q <= 2^26.

@@ -52,7 +52,9 @@ class _Model(ctypes.Structure):
                 ("M", ctypes.c_int), ("ell_m", ctypes.c_void_p), ("basis", ctypes.c_void_p),
                 ("t0", ctypes.c_double), ("dt", ctypes.c_double), ("det", ctypes.c_void_p),
                 ("d_ref", ctypes.c_double), ("R", ctypes.c_void_p), ("centre", ctypes.c_void_p),
-                ("stencil", ctypes.c_int)]
+                ("stencil", ctypes.c_int), ("sky", ctypes.c_int), ("dtensor", ctypes.c_void_p),
+                ("dpos", ctypes.c_void_p), ("tau", ctypes.c_void_p), ("gmst0", ctypes.c_double),
+                ("omega_e", ctypes.c_double)]
 
 
 def lib():
@@ -68,6 +70,8 @@ def lib():
             L.oracle_rbf_eval.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, dp, dp]
             L.oracle_amplitudes.argtypes = ([ctypes.POINTER(_Model), ctypes.c_int]
                                             + [ctypes.c_double] * 4 + [dp, dp])
+            L.oracle_sky_response.argtypes = ([ctypes.POINTER(_Model), ctypes.c_int]
+                                              + [ctypes.c_double] * 4 + [dp, dp, dp])
             L.oracle_loglike.argtypes = [ctypes.POINTER(_Model), ctypes.c_int, fp, fp,
                                          ctypes.c_int, dp, ctypes.c_int,
                                          ctypes.POINTER(ctypes.c_int)]
@@ -176,7 +180,7 @@ class Model:
     overlaps: per-(det, mode) SVD, one RBF fit for all columns, rotation."""
 
     def __init__(self, nodes, Z, sigma, rank, eps, tail_degree, modes, det, t0, dt,
-                 d_ref, metric=None, centre=None, stencil=10):
+                 d_ref, metric=None, centre=None, stencil=10, sky=None):
         nd, nm, N, M = Z.shape
         self.nodes = np.ascontiguousarray(nodes, dtype=np.float64)
         self.rank, self.eps, self.tail_degree = rank, float(eps), tail_degree
@@ -199,6 +203,28 @@ class Model:
                                            dtype=np.float64)
         self.ell_m = np.ascontiguousarray(np.array(self.modes, dtype=np.int32).reshape(-1))
         self.stencil = stencil
+        self.set_sky(sky)
+
+    def set_sky(self, sky):
+        """Sky mode (Eq. projected_h_td): sky = dict(tensor [n_det,3,3],
+        pos [n_det,3] (positions over c, seconds), tau [n_det] (channel epochs
+        relative to t_c, s), gmst0 (rad), omega (rad/s)); extrinsic rows then
+        carry (alpha, delta) in columns 5, 6.  None: frozen patterns (det)."""
+        nd = self.n_det
+        if sky is None:
+            self.sky = None
+            self._dtensor = np.zeros((nd, 3, 3))
+            self._dpos = np.zeros((nd, 3))
+            self._tau = np.zeros(nd)
+            self._gmst0 = self._omega = 0.0
+        else:
+            self.sky = sky
+            self._dtensor = np.ascontiguousarray(sky["tensor"], dtype=np.float64).reshape(nd, 3, 3)
+            self._dpos = np.ascontiguousarray(sky["pos"], dtype=np.float64).reshape(nd, 3)
+            tau = sky.get("tau")
+            self._tau = np.ascontiguousarray(np.zeros(nd) if tau is None else tau, dtype=np.float64)
+            self._gmst0 = float(sky["gmst0"])
+            self._omega = float(sky["omega"])
         self._c = self._struct()
 
     @classmethod
@@ -206,7 +232,8 @@ class Model:
         from workload.standin import node_overlaps, standin_sigma
         s = ev.spec
         return cls(ev.nodes, node_overlaps(ev), standin_sigma(ev, ev.nodes), s.rank, s.eps,
-                   s.tail_degree, s.modes, ev.det, s.t0, s.dt, s.d_ref, ev.metric, ev.centre)
+                   s.tail_degree, s.modes, ev.det, s.t0, s.dt, s.d_ref, ev.metric, ev.centre,
+                   sky=getattr(ev, "sky", None))
 
     @property
     def K(self):
@@ -221,7 +248,9 @@ class Model:
                       self.nodes.ctypes.data, self.W.ctypes.data, self.eps,
                       self.n_det, self.n_modes, self.rank, self.M, self.ell_m.ctypes.data,
                       self.basis.ctypes.data, self.t0, self.dt, self.det.ctypes.data,
-                      self.d_ref, self.R.ctypes.data, self.centre.ctypes.data, self.stencil)
+                      self.d_ref, self.R.ctypes.data, self.centre.ctypes.data, self.stencil,
+                      0 if self.sky is None else 1, self._dtensor.ctypes.data, self._dpos.ctypes.data,
+                      self._tau.ctypes.data, self._gmst0, self._omega)
 
     def rotate(self, theta):
         return (np.asarray(theta, np.float64) - self.centre) @ self.R.T
@@ -238,6 +267,13 @@ class Model:
         ci = np.empty(self.n_modes)
         lib().oracle_amplitudes(ctypes.byref(self._c), k, dL, cosi, psi, phic, _dp(cr), _dp(ci))
         return cr + 1j * ci
+
+    def sky_response(self, k, tc, alpha, delta, psi):
+        """(F+, Fx, dt) of channel k for one source (sky mode)."""
+        fp, fx, dt = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        lib().oracle_sky_response(ctypes.byref(self._c), int(k), float(tc), float(alpha), float(delta),
+                                  float(psi), ctypes.byref(fp), ctypes.byref(fx), ctypes.byref(dt))
+        return fp.value, fx.value, dt.value
 
     def loglike(self, intrinsic, extrinsic, nthreads: int = 0):
         """lnL [Q] (float64) for FP32 inputs intrinsic [Q,4], extrinsic [Q,5];

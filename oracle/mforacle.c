@@ -12,6 +12,8 @@
  *  - spin-weighted spherical harmonics ........... Eq. (h_spherical_harmonic_basis)
  *  - polarisations from negative-m modes ......... Eqs. (hplus_hcross_decomposed1/2)
  *  - frozen antenna patterns + detector delay .... Eq. (projected_h_fd)
+ *  - sky-dependent patterns F(alpha, delta, psi, t)
+ *    and geocentre-to-detector delays ............ Eqs. (projected_h_td/fd)
  *  - lnL = sum_k <h|d> - 1/2 ||h||^2 ............. Eqs. (logl_basic), (logl_complete)
  */
 #include <math.h>
@@ -36,6 +38,15 @@ typedef struct {
     const double *R;        /* [4][4] rows = metric eigenvectors                */
     const double *centre;   /* [4] ellipsoid centre                              */
     int stencil;            /* number of spline samples (10)                    */
+    /* sky mode (sky != 0): per query, detector k's antenna patterns and delay
+     * follow from the source's right ascension and declination (extrinsic
+     * columns 5 and 6) and the Earth's rotation angle at t_c + tau_k        */
+    int sky;
+    const double *dtensor;  /* [n_det][3][3] detector tensors, Earth-fixed frame */
+    const double *dpos;     /* [n_det][3] detector positions / c (seconds)       */
+    const double *tau;      /* [n_det] epoch of channel k relative to t_c (s)    */
+    double gmst0;           /* Greenwich sidereal angle at t_c = 0 (rad)         */
+    double omega_e;         /* Earth's sidereal rotation rate (rad/s)            */
 } oracle_model;
 
 /* ---------------------------------------------------------------- helpers */
@@ -152,19 +163,52 @@ void oracle_rbf_eval(const oracle_model *m, int Q, const double *x, double *f) {
     for (int q = 0; q < Q; ++q) rbf_eval_point(m, x + (size_t)q * 4, f + (size_t)q * m->K);
 }
 
-/* Per-mode complex amplitude multiplying the negative-m mode in detector k
- * (Eqs. hplus_hcross_decomposed1/2 substituted into Eq. projected_h_fd):
+/* Antenna patterns and delay of channel k for a source at right ascension
+ * alpha and declination delta with polarisation angle psi (Eq. projected_h_td
+ * at the epoch t_c + tau_k; the long-wavelength detector response):
+ *   h = GMST(t_c + tau_k) - alpha is the source's Greenwich hour angle,
+ *   w = (cos d cos h, -cos d sin h, sin d) the unit vector towards the source,
+ *   X0 = (-sin h, -cos h, 0) and Y0 = (-cos h sin d, sin h sin d, cos d) the
+ *   wave-frame axes at psi = 0, X = cos psi X0 + sin psi Y0,
+ *   Y = -sin psi X0 + cos psi Y0,
+ *   F+ = D : (X X - Y Y),  Fx = D : (X Y + Y X),  D the detector tensor,
+ *   dt = -(r . w) with r the detector position over c: the wave reaches a
+ *   detector on the source's side of the Earth before the geocentre. */
+void oracle_sky_response(const oracle_model *m, int k, double tc, double alpha, double delta,
+                         double psi, double *fp, double *fx, double *dt) {
+    double h = m->gmst0 + m->omega_e * (tc + m->tau[k]) - alpha;
+    double sd = sin(delta), cd = cos(delta), sh = sin(h), ch = cos(h);
+    double w[3] = {cd * ch, -cd * sh, sd};
+    double X0[3] = {-sh, -ch, 0.0};
+    double Y0[3] = {-ch * sd, sh * sd, cd};
+    double X[3], Y[3];
+    for (int i = 0; i < 3; ++i) {
+        X[i] = cos(psi) * X0[i] + sin(psi) * Y0[i];
+        Y[i] = -sin(psi) * X0[i] + cos(psi) * Y0[i];
+    }
+    const double *D = m->dtensor + (size_t)k * 9;
+    double p = 0.0, x = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            p += D[i * 3 + j] * (X[i] * X[j] - Y[i] * Y[j]);
+            x += D[i * 3 + j] * (X[i] * Y[j] + Y[i] * X[j]);
+        }
+    const double *r = m->dpos + (size_t)k * 3;
+    *fp = p;
+    *fx = x;
+    *dt = -(r[0] * w[0] + r[1] * w[1] + r[2] * w[2]);
+}
+
+/* Per-mode complex amplitude multiplying the negative-m mode in a detector
+ * with antenna patterns (F+, Fx) (Eqs. hplus_hcross_decomposed1/2
+ * substituted into Eq. projected_h_fd):
  *   h^k = sum_mu c_mu h_{l,-m},
  *   c_mu = (d_ref/d_L) * 1/2 [ (F+ + i Fx) Y_{l,-m} + (-1)^l (F+ - i Fx) conj(Y_{l,m}) ]
- * with F+(psi) = F+0 cos 2psi + Fx0 sin 2psi, Fx(psi) = -F+0 sin 2psi + Fx0 cos 2psi,
- * and Y = -2Y evaluated at (iota, phi_c). */
-void oracle_amplitudes(const oracle_model *m, int k, double dL, double cosi, double psi,
-                       double phic, double *c_re, double *c_im) {
+ * with Y = -2Y evaluated at (iota, phi_c). */
+static void amplitudes_from_f(const oracle_model *m, double fp, double fx, double dL, double cosi,
+                              double phic, double *c_re, double *c_im) {
     double iota = acos(cosi);
     double a = m->d_ref / dL;
-    double fp0 = m->det[k * 3 + 0], fx0 = m->det[k * 3 + 1];
-    double fp = fp0 * cos(2.0 * psi) + fx0 * sin(2.0 * psi);
-    double fx = -fp0 * sin(2.0 * psi) + fx0 * cos(2.0 * psi);
     for (int mu = 0; mu < m->n_modes; ++mu) {
         int l = m->ell_m[2 * mu], mm = m->ell_m[2 * mu + 1];
         double yn_re, yn_im, yp_re, yp_im;
@@ -178,6 +222,16 @@ void oracle_amplitudes(const oracle_model *m, int k, double dL, double cosi, dou
         c_re[mu] = 0.5 * a * (t1r + sl * t2r);
         c_im[mu] = 0.5 * a * (t1i + sl * t2i);
     }
+}
+
+/* Frozen antenna patterns of detector k (F+0, Fx0 at psi = 0):
+ * F+(psi) = F+0 cos 2psi + Fx0 sin 2psi, Fx(psi) = -F+0 sin 2psi + Fx0 cos 2psi. */
+void oracle_amplitudes(const oracle_model *m, int k, double dL, double cosi, double psi,
+                       double phic, double *c_re, double *c_im) {
+    double fp0 = m->det[k * 3 + 0], fx0 = m->det[k * 3 + 1];
+    double fp = fp0 * cos(2.0 * psi) + fx0 * sin(2.0 * psi);
+    double fx = -fp0 * sin(2.0 * psi) + fx0 * cos(2.0 * psi);
+    amplitudes_from_f(m, fp, fx, dL, cosi, phic, c_re, c_im);
 }
 
 /* Column of Re(C_i) for (det k, mode mu, coefficient i); Im follows at +rank. */
@@ -200,12 +254,21 @@ static int loglike_from_columns(const oracle_model *m, const double *f, const do
     double lnl = 0.0;
     int herm_bad = 0;
     for (int k = 0; k < m->n_det; ++k) {
-        double t = (double)ext[4] + m->det[k * 3 + 2];
+        double fp, fx, dtk;
+        if (m->sky) {
+            oracle_sky_response(m, k, ext[4], ext[5], ext[6], ext[2], &fp, &fx, &dtk);
+        } else {
+            double fp0 = m->det[k * 3 + 0], fx0 = m->det[k * 3 + 1];
+            fp = fp0 * cos(2.0 * ext[2]) + fx0 * sin(2.0 * ext[2]);
+            fx = -fp0 * sin(2.0 * ext[2]) + fx0 * cos(2.0 * ext[2]);
+            dtk = m->det[k * 3 + 2];
+        }
+        double t = (double)ext[4] + dtk;
         double s = (t - m->t0) / m->dt;
         int j = (int)floor(s);
         double u = s - j;
         if (j - half < 0 || j - half + S - 1 > m->M - 1) { *out = NAN; return 1; }
-        oracle_amplitudes(m, k, ext[0], ext[1], ext[2], ext[3], c_re, c_im);
+        amplitudes_from_f(m, fp, fx, ext[0], ext[1], ext[3], c_re, c_im);
         /* <h^k | d^k> = Re sum_mu conj(c_mu) z_mu(t_c + dt_k) */
         for (int mu = 0; mu < nm; ++mu) {
             /* Eq. (SVD): z(t_r) = sum_i C_i u_i(t_r) on the S stencil samples */
@@ -251,7 +314,7 @@ static int loglike_from_columns(const oracle_model *m, const double *f, const do
 }
 
 /* lnL for Q queries; intrinsic [Q][4] (sampler frame), extrinsic [Q][E]
- * = (d_L, cos iota, psi, phi_c, t_c).  Inputs are the FP32 values the GPU
+ * = (d_L, cos iota, psi, phi_c, t_c) and, in sky mode, (alpha, delta).  Inputs are the FP32 values the GPU
  * receives, promoted to FP64.  Returns the number of out-of-window queries;
  * *n_herm = queries whose c^H Sigma c had an imaginary part. */
 int oracle_loglike(const oracle_model *m, int Q, const float *intrinsic, const float *extrinsic,
@@ -267,9 +330,9 @@ int oracle_loglike(const oracle_model *m, int Q, const float *intrinsic, const f
         double *f = (double *)malloc(sizeof(double) * (size_t)m->K);
         #pragma omp for schedule(dynamic, 8)
         for (int q = 0; q < Q; ++q) {
-            double th[4], ex[5];
+            double th[4], ex[7] = {0, 0, 0, 0, 0, 0, 0};
             for (int i = 0; i < 4; ++i) th[i] = (double)intrinsic[(size_t)q * 4 + i];
-            for (int i = 0; i < 5; ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
+            for (int i = 0; i < (E < 7 ? E : 7); ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
             double x[4];
             rotate(m, th, x);
             rbf_eval_point(m, x, f);
@@ -297,8 +360,8 @@ int oracle_loglike_columns(const oracle_model *m, int Q, const double *F, const 
 #endif
     #pragma omp parallel for reduction(+:bad, herm) schedule(dynamic, 8)
     for (int q = 0; q < Q; ++q) {
-        double ex[5];
-        for (int i = 0; i < 5; ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
+        double ex[7] = {0, 0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < (E < 7 ? E : 7); ++i) ex[i] = (double)extrinsic[(size_t)q * E + i];
         const int st = loglike_from_columns(m, F + (size_t)q * m->K, ex, out + q);
         bad += st == 1;
         herm += st == 2;

@@ -63,6 +63,7 @@ def lib():
         L.mf_set_layout.argtypes = [vp, ip, ip, vp, ip]
         L.mf_set_basis.argtypes = [vp, vp, ip, dp, dp]
         L.mf_set_detectors.argtypes = [vp, vp, dp]
+        L.mf_set_sky.argtypes = [vp, vp, vp, vp, dp, dp, dp]
         L.mf_set_rotation.argtypes = [vp, vp, vp]
         L.mf_set_form.argtypes = [vp, ip]
         L.mf_loglike.argtypes = [vp, vp, vp, ip, ip, vp, vp]
@@ -174,9 +175,10 @@ class Interpolant:
 
     @classmethod
     def from_overlaps(cls, nodes, Z, sigma, rank, eps, modes, det, t0, dt, d_ref,
-                      metric=None, centre=None, tail_degree=1, form="fp32"):
+                      metric=None, centre=None, tail_degree=1, form="fp32", sky=None):
         """Full start-up on the GPU from node overlaps Z [n_det, n_modes, N, M]
-        (complex) and cross terms sigma [n_det, N, n_modes, n_modes]."""
+        (complex) and cross terms sigma [n_det, N, n_modes, n_modes]; sky: None
+        (frozen patterns det) or dict(tensor, pos, tau, gmst0, omega)."""
         nd, nm, N, M = Z.shape
         coef = np.empty((nd, nm, N, rank), np.complex128)
         basis = np.empty((nd, nm, rank, M), np.complex128)
@@ -186,7 +188,10 @@ class Interpolant:
         self = cls(nodes, pack_node_values(coef, sigma), eps, tail_degree)
         self.set_layout(nd, nm, modes, rank)
         self.set_basis(basis, t0, dt)
-        self.set_detectors(det, d_ref)
+        if sky is None:
+            self.set_detectors(det, d_ref)
+        else:
+            self.set_sky(sky["tensor"], sky["pos"], sky.get("tau"), sky["gmst0"], sky["omega"], d_ref)
         self.set_rotation(metric, centre)
         self.set_form(form)
         return self
@@ -204,6 +209,16 @@ class Interpolant:
     def set_detectors(self, det, d_ref):
         d = np.ascontiguousarray(det, dtype=np.float64)
         _check(lib().mf_set_detectors(self._h, _ptr(d), float(d_ref)), "mf_set_detectors")
+
+    def set_sky(self, tensor, pos, tau, gmst0, omega, d_ref):
+        """mf_set_sky: tensor [n_det,3,3], pos [n_det,3] (seconds), tau [n_det]
+        or None, gmst0 (rad), omega (rad/s); extrinsic rows then carry
+        (alpha, delta) in columns 5, 6."""
+        T = np.ascontiguousarray(tensor, dtype=np.float64)
+        P = np.ascontiguousarray(pos, dtype=np.float64)
+        t = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
+        _check(lib().mf_set_sky(self._h, _ptr(T), _ptr(P), None if t is None else _ptr(t), float(gmst0),
+                                float(omega), float(d_ref)), "mf_set_sky")
 
     def set_rotation(self, metric=None, centre=None):
         m = None if metric is None else np.ascontiguousarray(metric, dtype=np.float64)

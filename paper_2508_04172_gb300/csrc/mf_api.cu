@@ -184,7 +184,11 @@ EpiParams make_epi(const mf_handle *h) {
         e.ell[mu] = h->ell_m[2 * mu];
         e.em[mu] = h->ell_m[2 * mu + 1];
     }
-    for (int k = 0; k < h->n_det; ++k) {
+    // detectors and basis may not be set yet (mf_eval_columns needs only the
+    // layout): their fields then stay zero
+    const bool det_ok = h->have_det && h->det.size() >= (size_t)3 * h->n_det;
+    const bool basis_ok = h->have_basis && h->dt > 0;
+    for (int k = 0; k < h->n_det && det_ok && basis_ok; ++k) {
         e.fp0[k] = (float)h->det[3 * k];
         e.fx0[k] = (float)h->det[3 * k + 1];
         double off = (h->det[3 * k + 2] - h->t0) / h->dt;
@@ -192,7 +196,7 @@ EpiParams make_epi(const mf_handle *h) {
         e.J[k] = (int)J;
         e.frac[k] = (float)(off - J);
     }
-    e.inv_dt = (float)(1.0 / h->dt);
+    e.inv_dt = basis_ok ? (float)(1.0 / h->dt) : 0.f;
     e.d_ref = (float)h->d_ref;
     e.cubic = h->d_cubic;
     e.bad = h->d_bad;
@@ -201,6 +205,24 @@ EpiParams make_epi(const mf_handle *h) {
     e.n_pass = (int)h->passes.size();
     for (int g = 0; g < e.n_groups; ++g) e.groups[g] = h->groups[g];
     for (int p = 0; p < e.n_pass; ++p) e.passes[p] = h->passes[p];
+    e.sky = h->sky && det_ok ? 1 : 0;
+    if (e.sky) {
+        for (int k = 0; k < h->n_det; ++k) {
+            const double *D = h->sky_tensor.data() + 9 * k;
+            e.dten[k][0] = (float)D[0];
+            e.dten[k][1] = (float)D[4];
+            e.dten[k][2] = (float)D[8];
+            e.dten[k][3] = (float)(0.5 * (D[1] + D[3]));
+            e.dten[k][4] = (float)(0.5 * (D[2] + D[6]));
+            e.dten[k][5] = (float)(0.5 * (D[5] + D[7]));
+            for (int i = 0; i < 3; ++i) e.dpos[k][i] = (float)h->sky_pos[3 * k + i];
+            // reduced in FP64 so that the FP32 hour angle keeps its precision
+            double g = std::fmod(h->gmst0 + h->omega_e * h->sky_tau[k], 2.0 * M_PI);
+            if (g < 0) g += 2.0 * M_PI;
+            e.gk[k] = (float)g;
+        }
+        e.omega = (float)h->omega_e;
+    }
     return e;
 }
 
@@ -360,6 +382,7 @@ int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m, int ra
     h->have_layout = true;
     h->have_basis = false;
     h->have_det = false;
+    h->sky = false;
     return mf::prepare_form(h, h->form);
 }
 
@@ -381,6 +404,35 @@ int mf_set_detectors(mf_handle *h, const double *det, double d_ref) {
     if (!h->have_layout) return MF_E_STATE;
     h->det.assign(det, det + 3 * h->n_det);
     h->d_ref = d_ref;
+    h->sky = false;
+    h->have_det = true;
+    ++h->gen;
+    return MF_OK;
+}
+
+int mf_set_sky(mf_handle *h, const double *tensor, const double *pos, const double *tau, double gmst0,
+               double omega, double d_ref) {
+    if (!h || !tensor || !pos || !(d_ref > 0) || !std::isfinite(gmst0) || !std::isfinite(omega))
+        return MF_E_INVAL;
+    if (!h->have_layout) return MF_E_STATE;
+    const int nd = h->n_det;
+    for (int i = 0; i < 9 * nd; ++i)
+        if (!std::isfinite(tensor[i])) return MF_E_INVAL;
+    for (int i = 0; i < 3 * nd; ++i)
+        if (!std::isfinite(pos[i]) || std::fabs(pos[i]) > 1.0) return MF_E_INVAL;
+    for (int k = 0; tau && k < nd; ++k)
+        if (!std::isfinite(tau[k]) || std::fabs(tau[k]) > 1e7) return MF_E_INVAL;
+    h->sky_tensor.assign(tensor, tensor + 9 * nd);
+    h->sky_pos.assign(pos, pos + 3 * nd);
+    h->sky_tau.assign(nd, 0.0);
+    if (tau) h->sky_tau.assign(tau, tau + nd);
+    h->gmst0 = gmst0;
+    h->omega_e = omega;
+    // the frozen per-detector values are unused; the sample offset of t_c = 0
+    // is the same for every channel (its delay is added per query)
+    h->det.assign(3 * nd, 0.0);
+    h->d_ref = d_ref;
+    h->sky = true;
     h->have_det = true;
     ++h->gen;
     return MF_OK;
@@ -431,6 +483,7 @@ int mf_loglike(mf_handle *h, const float *intrinsic, const float *extrinsic, int
     if (!intrinsic || !extrinsic || !out_lnL) return MF_E_INVAL;
     if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;   // rows are read as float4
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
+    if (h->sky && E < 7) return MF_E_INVAL;   // (alpha, delta) columns needed
     cudaStream_t st = (cudaStream_t)stream;
     if (h->form == MF_FORM_MLP) {
         if (h->timing) MF_CUDA(cudaEventRecord(h->ev0, st));

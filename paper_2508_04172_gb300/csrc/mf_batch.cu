@@ -444,6 +444,8 @@ int mf_batch_create(mf_handle *const *hs, int n_events, const int *Q_plan, int a
 int mf_batch_loglike(mf_batch *b, const float *const *intrinsic, const float *const *extrinsic,
                      const int *Q, int E, float *const *out_lnL, void *stream) {
     if (!b || !intrinsic || !extrinsic || !Q || !out_lnL || E < 5) return MF_E_INVAL;
+    for (int e = 0; e < b->n; ++e)
+        if (b->hs[e]->sky && E < 7) return MF_E_INVAL;   // (alpha, delta) columns needed
     long long qtot = 0;
     for (int e = 0; e < b->n; ++e) {
         if (Q[e] < 0 || Q[e] > (1 << 26)) return MF_E_INVAL;

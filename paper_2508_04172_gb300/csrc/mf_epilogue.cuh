@@ -54,6 +54,7 @@ struct QueryExt {
     float c2p, s2p;     // cos 2psi, sin 2psi
     float cph, sph;     // cos phi_c, sin phi_c
     float tc;
+    float alpha, sd, cd;   // sky mode: right ascension, sin and cos of the declination
 };
 
 __device__ __forceinline__ QueryExt load_ext(const EpiParams &P, const float *ext, int E, int q) {
@@ -68,16 +69,55 @@ __device__ __forceinline__ QueryExt load_ext(const EpiParams &P, const float *ex
     x.cs = 0.5f * sqrtf(fmaxf(0.f, (1.f - ci) * (1.f + ci)));
     sincosf(2.f * psi, &x.s2p, &x.c2p);
     sincosf(phc, &x.sph, &x.cph);
+    x.alpha = 0.f;
+    x.sd = 0.f;
+    x.cd = 1.f;
+    if (P.sky) {
+        x.alpha = e[5];
+        sincosf(e[6], &x.sd, &x.cd);
+    }
     return x;
 }
 
+// Antenna patterns (F+, Fx) of detector k at the query's polarisation angle
+// and its geocentre-to-detector delay dt (Eqs. projected_h_td/fd).  Frozen
+// patterns: F(psi) = rotation of (F+0, Fx0) by 2 psi, the delay is in the
+// detector's sample offset (dt = 0 here).  Sky mode: with the hour angle
+// h = gk + omega t_c - alpha, the source direction w = (cos d cos h,
+// -cos d sin h, sin d) and the wave-frame axes at psi = 0, X0 = (-sin h,
+// -cos h, 0), Y0 = (-cos h sin d, sin h sin d, cos d), the detector tensor D
+// gives F+0 = X0.D.X0 - Y0.D.Y0 and Fx0 = 2 X0.D.Y0, which rotate with 2 psi
+// like the frozen ones; dt = -(r . w), r = position / c.
+__device__ __forceinline__ void det_response(const EpiParams &P, int k, const QueryExt &x, float &fp,
+                                             float &fx, float &dt) {
+    float fp0 = P.fp0[k], fx0 = P.fx0[k];
+    dt = 0.f;
+    if (P.sky) {
+        float sh, ch;
+        sincosf(P.gk[k] + P.omega * x.tc - x.alpha, &sh, &ch);
+        const float X[3] = {-sh, -ch, 0.f};
+        const float Y[3] = {-ch * x.sd, sh * x.sd, x.cd};
+        const float *D = P.dten[k];
+        // a.D.b for the symmetric D stored as (xx, yy, zz, xy, xz, yz)
+        auto quad = [&](const float (&a)[3], const float (&b)[3]) {
+            return D[0] * a[0] * b[0] + D[1] * a[1] * b[1] + D[2] * a[2] * b[2] +
+                   D[3] * (a[0] * b[1] + a[1] * b[0]) + D[4] * (a[0] * b[2] + a[2] * b[0]) +
+                   D[5] * (a[1] * b[2] + a[2] * b[1]);
+        };
+        fp0 = quad(X, X) - quad(Y, Y);
+        fx0 = 2.f * quad(X, Y);
+        dt = -(P.dpos[k][0] * x.cd * ch - P.dpos[k][1] * x.cd * sh + P.dpos[k][2] * x.sd);
+    }
+    fp = fp0 * x.c2p + fx0 * x.s2p;
+    fx = -fp0 * x.s2p + fx0 * x.c2p;
+}
+
 // c_k,mu = (d_ref/d_L)/2 e^{-i m phi_c} [F+ (A- + (-1)^l A+) + i Fx (A- - (-1)^l A+)]
-// (Eqs. hplus_hcross_decomposed1/2 in Eq. projected_h_fd).
+// (Eqs. hplus_hcross_decomposed1/2 in Eq. projected_h_fd), for the detector's
+// antenna patterns (fp, fx) at the query's polarisation angle.
 template <int NM>
-__device__ __forceinline__ void det_amplitudes(const EpiParams &P, int k, const QueryExt &x,
+__device__ __forceinline__ void det_amplitudes(const EpiParams &P, float fp, float fx, const QueryExt &x,
                                                float (&cre)[NM], float (&cim)[NM]) {
-    float fp = P.fp0[k] * x.c2p + P.fx0[k] * x.s2p;
-    float fx = -P.fp0[k] * x.s2p + P.fx0[k] * x.c2p;
 #pragma unroll
     for (int mu = 0; mu < NM; ++mu) {
         int l = P.ell[mu], m = P.em[mu];
@@ -99,11 +139,12 @@ __device__ __forceinline__ void det_amplitudes(const EpiParams &P, int k, const 
 }
 
 // Spline interval for detector k: sample j with t_c + dt_k in [t_j, t_j+1)
-// and the offset u in [0,1).  Returns false when the 10-sample window
-// j-4..j+5 leaves [0, M) (j is then clamped so that reads stay in range).
-__device__ __forceinline__ bool det_interval(const EpiParams &P, int k, float tc, int &j,
+// and the offset u in [0,1) (dt: the sky-dependent part of the delay, 0 for
+// frozen patterns).  Returns false when the 10-sample window j-4..j+5 leaves
+// [0, M) (j is then clamped so that reads stay in range).
+__device__ __forceinline__ bool det_interval(const EpiParams &P, int k, float tc, float dt, int &j,
                                              float &u) {
-    float v = fmaf(tc, P.inv_dt, P.frac[k]);
+    float v = fmaf(tc + dt, P.inv_dt, P.frac[k]);
     if (!(fabsf(v) < 1.0e7f)) {   // NaN / absurd times
         j = kStencilLo;
         u = 0.f;
@@ -134,8 +175,10 @@ __device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, co
             // control flow stays warp-uniform (the tcgen05 accessor loads with
             // .sync.aligned): an out-of-window query reads an in-range
             // interval and is flagged instead of skipped
-            if (!det_interval(P, cur, x.tc, j, u)) bad = true;
-            det_amplitudes<NM>(P, cur, x, cre, cim);
+            float fp, fx, dt;
+            det_response(P, cur, x, fp, fx, dt);
+            if (!det_interval(P, cur, x.tc, dt, j, u)) bad = true;
+            det_amplitudes<NM>(P, fp, fx, x, cre, cim);
         }
         if (G.kind == 0) {
             // Eq. (SVD) at t_c + dt_k: z = sum_i C_i S_i(u), S_i the spline of

@@ -59,6 +59,12 @@ struct EpiParams {
     Group groups[kMaxGroups];
     Pass passes[kMaxPass];
     int n_groups, n_pass;
+    // sky-dependent patterns (sky != 0): extrinsic columns 5, 6 = (alpha, delta)
+    int sky;
+    float dten[kMaxDet][6];  // detector tensor (xx, yy, zz, xy, xz, yz), Earth-fixed frame
+    float dpos[kMaxDet][3];  // detector position / c (seconds)
+    float gk[kMaxDet];       // sidereal angle at t_c = 0 of channel k: gmst0 + omega tau_k (mod 2 pi)
+    float omega;             // Earth's rotation rate (rad/s)
 };
 
 struct RotParams {
@@ -118,6 +124,12 @@ struct mf_handle {
     std::vector<int> ell_m;
     double t0 = 0, dt = 0, d_ref = 100.0;
     std::vector<double> det;       // [n_det][3]
+    // sky-dependent patterns (mf_set_sky)
+    bool sky = false;
+    std::vector<double> sky_tensor; // [n_det][3][3]
+    std::vector<double> sky_pos;    // [n_det][3] seconds
+    std::vector<double> sky_tau;    // [n_det] seconds
+    double gmst0 = 0, omega_e = 0;
     float4 *d_cubic = nullptr;      // spline cubic table (see EpiParams::cubic)
     // rotation
     double R[16] = {1,0,0,0, 0,1,0,0, 0,0,1,0, 0,0,0,1};

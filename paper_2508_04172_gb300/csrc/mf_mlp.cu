@@ -1019,6 +1019,7 @@ int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train, 
     if (n_held < 0 || (n_held > 0 && (!held_intrinsic || !held_extrinsic))) return MF_E_INVAL;
     if (((uintptr_t)train_intrinsic & 15) || ((uintptr_t)held_intrinsic & 15)) return MF_E_INVAL;
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
+    if (h->sky && E < 7) return MF_E_INVAL;
     cudaStream_t st = (cudaStream_t)stream;
     MF_CUDA(cudaStreamSynchronize(st));
     const mf_form prev = h->form;

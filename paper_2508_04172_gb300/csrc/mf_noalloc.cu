@@ -66,6 +66,7 @@ extern "C" int mf_loglike_noalloc(mf_handle *h, const float *intrinsic, const fl
     if (!intrinsic || !extrinsic || !out_lnL) return MF_E_INVAL;
     if ((uintptr_t)intrinsic & 15) return MF_E_INVAL;   // rows are read as float4
     if (!h->have_layout || !h->have_basis || !h->have_det) return MF_E_STATE;
+    if (h->sky && E < 7) return MF_E_INVAL;
     if (h->form != MF_FORM_FP32 || !h->d_W32) return MF_E_STATE;
     // the handle's buffers and the scratch address belong to h->dev
     int cur = -1;

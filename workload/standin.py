@@ -28,6 +28,19 @@ import numpy as np
 AMP = {(2, 2): 1.0, (2, 1): 0.3, (3, 3): 0.4, (4, 4): 0.2, (3, 2): 0.25}
 HM4 = ((2, 2), (2, 1), (3, 3), (4, 4))
 
+# Detector geometry of the sky-dependent workloads (input data, not the
+# method): vertices on a spherical Earth at the approximate latitude and
+# longitude of the Hanford, Livingston and Virgo sites and of a candidate
+# third-generation site, arm azimuths drawn from the seed.
+R_EARTH = 6.371e6              # m
+C_LIGHT = 299792458.0          # m/s
+OMEGA_EARTH = 7.292115e-5      # sidereal rotation rate, rad/s
+SITES = {"H": (46.455, -119.408), "L": (30.563, -90.774), "V": (43.631, 10.504),
+         "E": (40.52, 9.42)}
+# emission epochs (s before coalescence) of four frequency bands of a signal
+# that stays in band for ~50 minutes (third-generation detector)
+ET_BANDS = (-2400.0, -900.0, -240.0, -30.0)
+
 
 def eps_rule(n_nodes: int) -> float:
     """Gaussian shape parameter used for C1..C4 (the paper leaves it to the
@@ -55,6 +68,8 @@ class Spec:
     d_ref: float = 100.0
     det_kind: str = "seeded"   # "optimal" (C0), "seeded" (HLV-like), "et" (C4)
     seed: int = 0
+    sky: str = ""              # "": frozen patterns; "hlv" / "et": per-query (alpha, delta)
+    epochs: tuple = ()         # per channel epoch offsets (s) of frequency bands, sky "et"
 
     @property
     def n_modes(self) -> int:
@@ -70,6 +85,12 @@ class Spec:
     def t0(self) -> float:
         return -(self.M // 2) * self.dt
 
+    @property
+    def E(self) -> int:
+        """Extrinsic columns per query: (d_L, cos iota, psi, phi_c, t_c) and,
+        with sky-dependent patterns, (alpha, delta)."""
+        return 7 if self.sky else 5
+
 
 CONFIGS = {
     "C0": Spec("C0", 1, ((2, 2),), 8, 128, 200, 1024, 1.5, rotate=False,
@@ -78,6 +99,14 @@ CONFIGS = {
     "C2": Spec("C2", 3, HM4, 40, 512, 4000, 262144, eps_rule(4000), seed=2000),
     "C4": Spec("C4", 1, HM4, 80, 2048, 8000, 1000000, eps_rule(8000),
                det_kind="et", seed=4000),
+    # sky-dependent antenna patterns and delays (extrinsic alpha, delta per query)
+    "C1S": Spec("C1S", 3, HM4, 20, 512, 1500, 65536, eps_rule(1500), seed=1100, sky="hlv"),
+    "C4S": Spec("C4S", 1, HM4, 80, 2048, 8000, 1000000, eps_rule(8000), det_kind="et",
+                seed=4100, sky="et"),
+    # time-dependent patterns of a long third-generation signal: one detector,
+    # four frequency-band channels, each with its own epoch of Earth rotation
+    "C4T": Spec("C4T", 4, HM4, 40, 2048, 4000, 262144, eps_rule(4000), det_kind="et",
+                seed=4200, sky="et", epochs=ET_BANDS),
 }
 
 
@@ -128,6 +157,37 @@ def _canonical_rotation(rng) -> np.ndarray:
     return R
 
 
+def site_geometry(lat_deg: float, lon_deg: float, azimuth: float, opening: float):
+    """Detector tensor D = (u u^T - v v^T) / 2 and vertex position / c for an
+    interferometer on a spherical Earth: arms u, v in the local horizontal
+    plane at `azimuth` and `azimuth + opening` from east (radians)."""
+    la, lo = math.radians(lat_deg), math.radians(lon_deg)
+    east = np.array([-math.sin(lo), math.cos(lo), 0.0])
+    north = np.array([-math.sin(la) * math.cos(lo), -math.sin(la) * math.sin(lo), math.cos(la)])
+    up = np.array([math.cos(la) * math.cos(lo), math.cos(la) * math.sin(lo), math.sin(la)])
+    u = math.cos(azimuth) * east + math.sin(azimuth) * north
+    v = math.cos(azimuth + opening) * east + math.sin(azimuth + opening) * north
+    return 0.5 * (np.outer(u, u) - np.outer(v, v)), R_EARTH * up / C_LIGHT
+
+
+def make_sky(spec, rng) -> dict:
+    """Detector tensors, positions / c, channel epochs and the sidereal angle
+    at t_c = 0 of a sky-dependent workload."""
+    if spec.sky == "hlv":
+        sites = [SITES[c] for c in "HLV"][:spec.n_det]
+        geo = [site_geometry(la, lo, rng.uniform(0, np.pi), np.pi / 2) for la, lo in sites]
+        tau = np.zeros(spec.n_det)
+    elif spec.sky == "et":
+        g = site_geometry(*SITES["E"], rng.uniform(0, np.pi), np.pi / 3)
+        geo = [g] * spec.n_det
+        tau = np.array(spec.epochs if spec.epochs else (0.0,) * spec.n_det, dtype=np.float64)
+        assert tau.shape == (spec.n_det,)
+    else:
+        raise ValueError(spec.sky)
+    return {"tensor": np.stack([d for d, _ in geo]), "pos": np.stack([r for _, r in geo]),
+            "tau": tau, "gmst0": float(rng.uniform(0, 2 * np.pi)), "omega": OMEGA_EARTH}
+
+
 @dataclasses.dataclass
 class Event:
     spec: Spec
@@ -141,6 +201,7 @@ class Event:
     metric: np.ndarray | None  # [4,4] SPD or None (identity rotation)
     centre: np.ndarray         # [4]
     R0: np.ndarray             # [4,4] rows = eigenvectors, ascending eigenvalue
+    sky: dict | None = None    # sky-dependent geometry (make_sky) or None
 
     @property
     def t_grid(self) -> np.ndarray:
@@ -184,7 +245,8 @@ def make_event(spec: Spec) -> Event:
         centre = rng.uniform(-0.5, 0.5, 4)
     else:
         R0, metric, centre = np.eye(4), None, np.zeros(4)
-    return Event(spec, nodes, tau, beta, phi0, gamma, s_det, det, metric, centre, R0)
+    sky = make_sky(spec, np.random.default_rng(spec.seed + 5)) if spec.sky else None
+    return Event(spec, nodes, tau, beta, phi0, gamma, s_det, det, metric, centre, R0, sky)
 
 
 def standin_z(ev: Event, k: int, j: int, y: np.ndarray, t: np.ndarray,
@@ -234,15 +296,20 @@ def make_queries(ev: Event, Q: int, seed: int | None = None, radius: float = 0.9
                  tc_range: float = 5e-3):
     """Q queries: Delta-e points uniform in the ball of radius 0.9, mapped to the
     sampler frame; extrinsics (d_L, cos iota, psi, phi_c, t_c) drawn as in the
-    paper's prior table restricted to the config ranges.  Returns FP32 arrays
-    intrinsic [Q,4], extrinsic [Q,5] (what both implementations consume)."""
+    paper's prior table restricted to the config ranges, and for sky-dependent
+    workloads (alpha, delta) isotropic on the sky (alpha uniform, sin delta
+    uniform).  Returns FP32 arrays intrinsic [Q,4], extrinsic [Q,E] (what both
+    implementations consume)."""
     rng = np.random.default_rng(ev.spec.seed + 17 if seed is None else seed)
     x = ball(rng, Q, r=radius)
     theta = ev.centre[None, :] + x @ ev.R0
-    ext = np.empty((Q, 5))
+    ext = np.empty((Q, ev.spec.E))
     ext[:, 0] = rng.uniform(100.0, 400.0, Q)
     ext[:, 1] = rng.uniform(-1.0, 1.0, Q)
     ext[:, 2] = rng.uniform(0.0, np.pi, Q)
     ext[:, 3] = rng.uniform(0.0, 2 * np.pi, Q)
     ext[:, 4] = rng.uniform(-tc_range, tc_range, Q)
+    if ev.spec.sky:
+        ext[:, 5] = rng.uniform(0.0, 2 * np.pi, Q)
+        ext[:, 6] = np.arcsin(rng.uniform(-1.0, 1.0, Q))
     return theta.astype(np.float32), ext.astype(np.float32)
