@@ -377,9 +377,11 @@ MF_API int mf_mlp_query(const mf_mlp *m, const char *key, double *value);
  * mf_loglike then evaluates the network (chunks of 65536 queries: input
  * layer, hidden GEMMs, final GEMM fused with the lnL epilogue) and sends
  * queries with |x| beyond the training radius (r_gate; by default the
- * largest training |x|) to the FP32 RBF path
- * (the call synchronises its stream once to size that launch); if the gate
- * failed, the RBF path serves every query.  mf_query: "fallback_rate",
+ * largest training |x|) to the FP32 RBF path: those queries are compacted
+ * on the device and the RBF launch reads their count there, so the call
+ * never waits for the GPU (mf_query "fallback_rate" reads the last call's
+ * count and waits for it); if the gate failed, the RBF path serves every
+ * query.  mf_query: "fallback_rate",
  * "surrogate_gate", "surrogate_heldout_max" / "_median" / "_p99",
  * "surrogate_train_ms", "surrogate_label_ms", "surrogate_gate_ms",
  * "surrogate_loss", "surrogate_r_gate", "surrogate_n_params".

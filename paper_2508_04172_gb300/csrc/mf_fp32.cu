@@ -13,6 +13,8 @@
 // fixed order (so results are bitwise reproducible).
 #include "mf_epilogue.cuh"
 
+#include <algorithm>
+
 namespace mf {
 
 namespace {
@@ -41,20 +43,21 @@ __device__ __forceinline__ void rotate_query(const RotParams &rot, const float *
                 rot.R[4 * i + 3] * d[3];
 }
 
+// One (query tile, column pass) work item.
 template <int NM, bool COLUMNS>
-__global__ void __launch_bounds__(kThreads, 2)
-fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q, int E,
-            int N, int P, int Nk, const float *__restrict__ W, int Kdev,
-            const float4 *__restrict__ nodes_s, RotParams rot, EpiParams epi,
-            float *__restrict__ out, float *__restrict__ partial,
-            const int *__restrict__ user_of_dev, const float *__restrict__ colscale, int Kuser) {
+__device__ __forceinline__ void fp32_tile(const float *__restrict__ intr, const float *__restrict__ ext, int Q,
+                                          int E, int N, int P, int Nk, const float *__restrict__ W, int Kdev,
+                                          const float4 *__restrict__ nodes_s, const RotParams &rot,
+                                          const EpiParams &epi, float *__restrict__ out,
+                                          float *__restrict__ partial, const int *__restrict__ user_of_dev,
+                                          const float *__restrict__ colscale, int Kuser, int tile) {
     extern __shared__ __align__(16) float smem[];
     const int tid = threadIdx.x;
     const int pass = blockIdx.y;
     const Pass ps = epi.passes[pass];
     const int width = ps.width;
     const int jw = width >> 4;
-    const int q0 = blockIdx.x * kTile;
+    const int q0 = tile * kTile;
 
     float4 *xs_s = reinterpret_cast<float4 *>(smem);            // [128] prescaled x
     float4 *xu_s = xs_s + kTile;                                 // [128] unscaled x
@@ -172,9 +175,35 @@ fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q
     }
 }
 
+// dQ == nullptr: one tile per CTA (grid.x = tiles of Q).  Otherwise the batch
+// size is read on the device (a count another kernel produced, so that the
+// host need not wait for it): the CTAs stride over the tiles of *dQ queries.
+template <int NM, bool COLUMNS>
+__global__ void __launch_bounds__(kThreads, 2)
+fp32_kernel(const float *__restrict__ intr, const float *__restrict__ ext, int Q, int E,
+            int N, int P, int Nk, const float *__restrict__ W, int Kdev,
+            const float4 *__restrict__ nodes_s, RotParams rot, EpiParams epi,
+            float *__restrict__ out, float *__restrict__ partial,
+            const int *__restrict__ user_of_dev, const float *__restrict__ colscale, int Kuser,
+            const int *__restrict__ dQ) {
+    if (!dQ) {
+        fp32_tile<NM, COLUMNS>(intr, ext, Q, E, N, P, Nk, W, Kdev, nodes_s, rot, epi, out, partial, user_of_dev,
+                               colscale, Kuser, blockIdx.x);
+        return;
+    }
+    const int Qd = min(*dQ, Q);
+    const int nt = (Qd + kTile - 1) / kTile;
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        fp32_tile<NM, COLUMNS>(intr, ext, Qd, E, N, P, Nk, W, Kdev, nodes_s, rot, epi, out, partial,
+                               user_of_dev, colscale, Kuser, t);
+        __syncthreads();   // shared memory is reused by the next tile
+    }
+}
+
 __global__ void combine_kernel(const float *__restrict__ partial, int n_pass, int Q,
-                               float *__restrict__ out, unsigned long long *bad) {
+                               float *__restrict__ out, unsigned long long *bad, const int *__restrict__ dQ) {
     int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (dQ) Q = min(*dQ, Q);
     if (q >= Q) return;
     float s = 0.f;
     for (int p = 0; p < n_pass; ++p) s += partial[(size_t)p * Q + q];
@@ -184,7 +213,7 @@ __global__ void combine_kernel(const float *__restrict__ partial, int n_pass, in
 
 template <int NM, bool COLUMNS>
 int launch_fp32_nm(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-                   cudaStream_t st, float *partial, int Kuser) {
+                   cudaStream_t st, float *partial, int Kuser, const int *dQ) {
     EpiParams epi = make_epi(h);
     RotParams rot = make_rot(h);
     int maxw = 0;
@@ -195,23 +224,30 @@ int launch_fp32_nm(mf_handle *h, const float *intr, const float *ext, int Q, int
     size_t bytes = sizeof(float) * (gemm > epis ? gemm : epis);
     auto kern = fp32_kernel<NM, COLUMNS>;
     MF_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    dim3 grid((Q + kTile - 1) / kTile, (unsigned)h->passes.size());
+    int tiles = (Q + kTile - 1) / kTile;
+    if (dQ) {   // at most two resident waves of CTAs stride over the device-counted tiles
+        int sms = 0, dev = 0;
+        MF_CUDA(cudaGetDevice(&dev));
+        MF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        tiles = std::max(1, std::min(tiles, 2 * sms));
+    }
+    dim3 grid((unsigned)tiles, (unsigned)h->passes.size());
     kern<<<grid, kThreads, bytes, st>>>(intr, ext, Q, E, h->N, h->P, h->Nk, h->d_W32, h->Kdev,
                                         h->d_nodes_s, rot, epi, out, partial, h->d_user_of_dev,
-                                        nullptr, Kuser);
+                                        nullptr, Kuser, dQ);
     MF_CUDA(cudaGetLastError());
     return MF_OK;
 }
 
 template <bool COLUMNS>
 int launch_fp32_any(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-                    cudaStream_t st, float *partial, int Kuser) {
+                    cudaStream_t st, float *partial, int Kuser, const int *dQ) {
     switch (h->n_modes) {
-        case 1: return launch_fp32_nm<1, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser);
-        case 2: return launch_fp32_nm<2, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser);
-        case 3: return launch_fp32_nm<3, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser);
-        case 4: return launch_fp32_nm<4, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser);
-        case 5: return launch_fp32_nm<5, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser);
+        case 1: return launch_fp32_nm<1, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser, dQ);
+        case 2: return launch_fp32_nm<2, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser, dQ);
+        case 3: return launch_fp32_nm<3, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser, dQ);
+        case 4: return launch_fp32_nm<4, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser, dQ);
+        case 5: return launch_fp32_nm<5, COLUMNS>(h, intr, ext, Q, E, out, st, partial, Kuser, dQ);
         default: return MF_E_NOTIMPL;
     }
 }
@@ -219,17 +255,17 @@ int launch_fp32_any(mf_handle *h, const float *intr, const float *ext, int Q, in
 }  // namespace
 
 int launch_fp32(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-                cudaStream_t st, float *partial) {
-    return launch_fp32_any<false>(h, intr, ext, Q, E, out, st, partial, 0);
+                cudaStream_t st, float *partial, const int *dQ) {
+    return launch_fp32_any<false>(h, intr, ext, Q, E, out, st, partial, 0, dQ);
 }
 
 int launch_fp32_columns(mf_handle *h, const float *intr, int Q, float *out, cudaStream_t st) {
-    return launch_fp32_any<true>(h, intr, nullptr, Q, 0, out, st, nullptr, h->K);
+    return launch_fp32_any<true>(h, intr, nullptr, Q, 0, out, st, nullptr, h->K, nullptr);
 }
 
 int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStream_t st,
-                   unsigned long long *bad) {
-    combine_kernel<<<(Q + 255) / 256, 256, 0, st>>>(partial, n_pass, Q, out, bad);
+                   unsigned long long *bad, const int *dQ) {
+    combine_kernel<<<(Q + 255) / 256, 256, 0, st>>>(partial, n_pass, Q, out, bad, dQ);
     MF_CUDA(cudaGetLastError());
     return MF_OK;
 }

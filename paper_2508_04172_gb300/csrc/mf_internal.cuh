@@ -187,14 +187,15 @@ int build_cubic_table(mf_handle *h, const double *basis_host);  // spline cubics
 EpiParams make_epi(const mf_handle *h);
 RotParams make_rot(const mf_handle *h);
 // kernels launchers
+// dQ != nullptr: the batch size is *dQ (<= Q), read on the device
 int launch_fp32(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-                cudaStream_t st, float *partial);
+                cudaStream_t st, float *partial, const int *dQ = nullptr);
 int launch_fp32_columns(mf_handle *h, const float *intr, int Q, float *out, cudaStream_t st);
 // cols != nullptr: interpolated columns only, out [Q][K] (mf_eval_columns)
 int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
               cudaStream_t st, float *partial, float *cols = nullptr);
 int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStream_t st,
-                   unsigned long long *bad);
+                   unsigned long long *bad, const int *dQ = nullptr);
 int launch_tc2(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
                cudaStream_t st, float *partial, float *cols = nullptr);
 int tc2_pass_max();

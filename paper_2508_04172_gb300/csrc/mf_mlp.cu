@@ -569,6 +569,8 @@ struct mf_surrogate {
     int last_launches = 0;                        // kernels launched by the last mf_loglike
     float *d_colbuf = nullptr;                    // [chunk][Kdev] network columns (mf_eval_columns)
     size_t colbuf_cap = 0;
+    bool fb_pending = false;                      // fallback count of the last call still on the device
+    int fb_Q = 0;
 };
 
 namespace mf {
@@ -911,6 +913,7 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
     const int np = (int)h->passes.size();
     if (!s->gate && !force_net) {   // held-out gate failed: the RBF path serves everything
         s->fallback_rate = 1.0;
+        s->fb_pending = false;
         s->last_launches = np > 1 ? 2 : 1;
         int rc = ensure_infer(s, 1, Q, E, np);
         if (rc) return rc;
@@ -966,27 +969,28 @@ int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, 
     }
     if (force_net) {
         s->fallback_rate = 0.0;
+        s->fb_pending = false;
         return MF_OK;
     }
-    // queries outside the training radius: plain RBF (the count sizes that launch)
-    int nfb = 0;
-    MF_CUDA(cudaMemcpyAsync(&nfb, s->d_count, sizeof(int), cudaMemcpyDeviceToHost, st));
-    MF_CUDA(cudaStreamSynchronize(st));
-    s->fallback_rate = (double)nfb / (double)Q;
-    if (nfb == 0) return MF_OK;
+    // queries outside the training radius: compacted on the device and
+    // evaluated by the plain RBF path, whose launch reads their count on the
+    // device (no host synchronisation: the call stays asynchronous and can be
+    // captured in a CUDA graph); results are scattered back in place
     MF_CUDA(cudaMemsetAsync(s->d_count + 1, 0, 4, st));
     sur_compact_kernel<<<(Q + 255) / 256, 256, 0, st>>>(s->d_flag, Q, intr, ext, E, s->d_count + 1, s->d_list,
                                                         s->d_ci, s->d_ce);
     MF_CUDA(cudaGetLastError());
-    rc = launch_fp32(h, s->d_ci, s->d_ce, nfb, E, s->d_co, st, np > 1 ? s->d_cpart : nullptr);
+    rc = launch_fp32(h, s->d_ci, s->d_ce, Q, E, s->d_co, st, np > 1 ? s->d_cpart : nullptr, s->d_count + 1);
     if (rc) return rc;
     if (np > 1) {
-        rc = launch_combine(s->d_cpart, np, nfb, s->d_co, st, h->d_bad);
+        rc = launch_combine(s->d_cpart, np, Q, s->d_co, st, h->d_bad, s->d_count + 1);
         if (rc) return rc;
     }
-    sur_scatter_kernel<<<(nfb + 255) / 256, 256, 0, st>>>(s->d_list, s->d_count, s->d_co, out);
+    sur_scatter_kernel<<<(Q + 255) / 256, 256, 0, st>>>(s->d_list, s->d_count + 1, s->d_co, out);
     MF_CUDA(cudaGetLastError());
     s->last_launches += 3 + (np > 1 ? 1 : 0);
+    s->fb_pending = true;     // the rate is read from the device count when queried
+    s->fb_Q = Q;
     return MF_OK;
 }
 
@@ -1157,8 +1161,15 @@ int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train, 
 
 namespace mf {
 int surrogate_query(const mf_handle *h, const std::string &k, double *v) {
-    const mf_surrogate *s = h->sur;
+    mf_surrogate *s = h->sur;
     if (!s) return MF_E_STATE;
+    if (k == "fallback_rate" && s->fb_pending) {
+        // the count of the last call, once the device has produced it
+        int n = 0;
+        MF_CUDA(cudaMemcpy(&n, s->d_count + 1, sizeof(int), cudaMemcpyDeviceToHost));
+        s->fallback_rate = s->fb_Q > 0 ? (double)n / (double)s->fb_Q : 0.0;
+        s->fb_pending = false;
+    }
     if (k == "fallback_rate") *v = s->fallback_rate;
     else if (k == "surrogate_gate") *v = s->gate ? 1.0 : 0.0;
     else if (k == "surrogate_heldout_max") *v = s->ho_max;

@@ -7,8 +7,10 @@
 //     node-by-time matrix, projection C = Z V.
 //   * 4x4 metric eigendecomposition (cyclic Jacobi) for the Delta-e rotation
 //     (Sec. II D) and the 10-sample not-a-knot spline operator (Sec. II D).
-// Dense factorizations use cuSOLVER and the Gram/projection GEMMs cuBLAS; the
-// matrix assembly, Schur step, iterations and small solves are kernels here.
+// The Cholesky factorisation and triangular solves are this library's own
+// FP64 kernels (mf_chol.cu); the SVD uses cuSOLVER and its projection GEMM
+// cuBLAS; the matrix assembly, Schur step, iterations and small solves are
+// kernels here.
 #include "mf_internal.cuh"
 
 #include <cublas_v2.h>
@@ -23,6 +25,8 @@
 #include <new>
 
 namespace mf {
+int chol_factor(double *A, int N, double *diag0, int *err, cudaStream_t st);
+int chol_solve(const double *L, int N, double *X, int ncols, cudaStream_t st);
 namespace {
 
 struct Libs {
@@ -409,11 +413,8 @@ int compute_stencil(mf_handle *h) {
 int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
     const int N = h->N, K = h->K, P = h->P;
     const int ncols = K + P;
-    Libs L;
-    MF_LIBCALL(cusolverDnCreate(&L.sol));
-    MF_LIBCALL(cusolverDnSetStream(L.sol, st));
-    DevBuf<double> A, B, F, T, b, x, y, nrm, work, cancel, fmax_d;
-    DevBuf<int> info, err;
+    DevBuf<double> A, B, F, T, b, x, y, nrm, cancel, fmax_d, diag0;
+    DevBuf<int> err, cerr;
     MF_CUDA(A.alloc((size_t)N * N));
     MF_CUDA(B.alloc((size_t)N * ncols));
     MF_CUDA(F.alloc((size_t)N * K));
@@ -422,11 +423,13 @@ int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
     MF_CUDA(x.alloc(N));
     MF_CUDA(y.alloc(N));
     MF_CUDA(nrm.alloc(1));
-    MF_CUDA(info.alloc(1));
     MF_CUDA(err.alloc(1));
+    MF_CUDA(cerr.alloc(1));
     MF_CUDA(fmax_d.alloc(1));
+    MF_CUDA(diag0.alloc(N));
     MF_CUDA(cudaMemcpyAsync(F.p, F_host, sizeof(double) * (size_t)N * K, cudaMemcpyHostToDevice, st));
     MF_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    MF_CUDA(cudaMemsetAsync(cerr.p, 0, sizeof(int), st));
 
     const double eps2 = h->eps * h->eps;
     assemble_phi64<<<dim3((N + 255) / 256, N), 256, 0, st>>>(h->d_nodes64, N, eps2, A.p);
@@ -441,29 +444,29 @@ int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaMemcpyAsync(&lmax, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
 
-    int lwork = 0;
-    MF_LIBCALL(cusolverDnDpotrf_bufferSize(L.sol, CUBLAS_FILL_MODE_LOWER, N, A.p, N, &lwork));
-    MF_CUDA(work.alloc((size_t)lwork + 1));
-    MF_LIBCALL(cusolverDnDpotrf(L.sol, CUBLAS_FILL_MODE_LOWER, N, A.p, N, work.p, lwork, info.p));
-    int hinfo = 0;
-    MF_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    // Phi = L L^T (FP64, blocked right-looking); a pivot that is not positive
+    // beyond rounding means Phi is numerically singular
+    int rc = chol_factor(A.p, N, diag0.p, cerr.p, st);
+    if (rc) return rc;
+    int hc = 0;
+    MF_CUDA(cudaMemcpyAsync(&hc, cerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MF_CUDA(cudaStreamSynchronize(st));
-    if (hinfo != 0) return MF_E_ILLCOND;
+    if (hc != 0) return MF_E_ILLCOND;
 
     // lambda_min by inverse iteration with the Cholesky factor
     fill64<<<(N + 255) / 256, 256, 0, st>>>(x.p, N, 1.0 / std::sqrt((double)N));
     double inv = 0.0;
     for (int it = 0; it < 40; ++it) {
         MF_CUDA(cudaMemcpyAsync(y.p, x.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-        MF_LIBCALL(cusolverDnDpotrs(L.sol, CUBLAS_FILL_MODE_LOWER, N, 1, A.p, N, y.p, N, info.p));
+        rc = chol_solve(A.p, N, y.p, 1, st);
+        if (rc) return rc;
         normalize64<<<1, 256, 0, st>>>(y.p, N, x.p, nrm.p);
     }
-    MF_CUDA(cudaMemcpyAsync(&inv, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-
     // solve Phi X = [F | P]
     assemble_rhs<<<dim3((N + 255) / 256, ncols), 256, 0, st>>>(F.p, h->d_nodes64, N, K, P, B.p);
     MF_CUDA(cudaGetLastError());
-    MF_LIBCALL(cusolverDnDpotrs(L.sol, CUBLAS_FILL_MODE_LOWER, N, ncols, A.p, N, B.p, N, info.p));
+    rc = chol_solve(A.p, N, B.p, ncols, st);
+    if (rc) return rc;
     MF_CUDA(cudaMalloc((void **)&h->d_W64, sizeof(double) * (size_t)(N + P) * K));
     if (P > 0) {
         tail_dots<<<ncols, 256, 0, st>>>(B.p, h->d_nodes64, N, P, T.p, ncols);

@@ -133,3 +133,48 @@ def test_surrogate_speedup_over_plain_rbf(c4):
     finally:
         m.set_form("fp32")
     assert t_rbf / t_mlp > 5.0, (t_rbf, t_mlp)
+
+
+def test_surrogate_form_call_captures_into_a_cuda_graph(c4):
+    """The surrogate form sizes its RBF fallback launch on the device, so a
+    whole call (network, fallback for queries beyond the training radius,
+    scatter) enqueues without waiting for the GPU and can be captured; the
+    replayed graph gives bit-identical lnL to a direct call."""
+    import torch
+    m, st = c4
+    ev = _cases.event("C4")
+    th, ex = _cases.queries("C4", 5000, seed=45)
+    d = th.astype(np.float64) - ev.centre
+    r = np.linalg.norm(d, axis=1, keepdims=True)
+    far = np.zeros(len(th), bool)
+    far[::5] = True                      # a fifth beyond the training radius
+    d[far] *= 0.95 / r[far]
+    th = (ev.centre + d).astype(np.float32)
+    t, e = _cuda(th), _cuda(ex)
+    m.set_form("mlp")
+    try:
+        direct = m.loglike(t, e).clone()
+        torch.cuda.synchronize()
+        rate = m.query("fallback_rate")
+        out = torch.full_like(direct, float("nan"))
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            m.loglike(t, e, out=out)         # warm-up on the capture-side stream
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        out.fill_(float("nan"))
+        with torch.cuda.graph(g):
+            m.loglike(t, e, out=out)
+        torch.cuda.synchronize()
+        assert torch.isnan(out).all()        # captured, not run
+        for _ in range(2):
+            out.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(out, direct)
+        assert m.sync_status()[0] == 0
+    finally:
+        m.set_form("fp32")
+    assert abs(rate - far.mean()) <= 3.0 / len(th)    # (a stray in-ball query may sit beyond r_gate)
