@@ -458,6 +458,43 @@ def run_kernels_only(args):
               flush=True)
 
 
+def run_sampler(args):
+    """A nested-sampling run over the meshfree likelihood (the paper's
+    settings: 1000 live points, random walks of 150 steps, dlogz 0.1) on the
+    GPU, next to the oracle's sampler over the FP64 oracle likelihood on the
+    host cores; prints one JSON line (not the headline metric)."""
+    import torch
+    import paper_2508_04172_gb300 as mf
+    import oracle  # noqa: F401  (test infrastructure: CPU comparison only)
+    from oracle import nested as ons
+    torch.cuda.set_device(0)
+    spec, ev, m, th, ex = build_workload(args.config, 0)
+    form = args.forms.split(",")[0] if args.forms and "," not in args.forms else "fp16_3term"
+    m.set_form(form)
+    kw = dict(n_live=1000, batch=100, walks=150, dlogz=0.1, r_ball=0.9, seed=1)
+    mf.nested_sample(m, **dict(kw, max_iter=2))          # warm-up (kernels, buffers)
+    g = mf.nested_sample(m, **kw)
+    w, neff = mf.reweight(g["logwt"])
+    line = {"metric": "nested-sampling run over the meshfree lnL (GPU driver)", "config": {
+        "workload": workload_name(spec), "form": form, "n_live": kw["n_live"], "batch": kw["batch"],
+        "walks": kw["walks"], "dlogz": kw["dlogz"]},
+        "gpu": {"wall_s": round(g["wall_ms"] / 1e3, 3), "n_like": g["n_like"],
+                "lnl_evals_per_s": round(g["n_like"] / (g["wall_ms"] / 1e3), 1), "logz": g["logz"],
+                "logz_err": g["logz_err"], "info": g["info"], "iterations": g["iterations"],
+                "accept": g["accept"], "n_samples": g["n_samples"], "n_eff": neff}}
+    if args.cpu_budget > 0:
+        om = oracle.Model.from_event(ev)
+        t = time.perf_counter()
+        o = ons.nested_sample(lambda a, b: om.loglike(a, b), dim=11 if spec.sky else 9, R=om.R,
+                              centre=om.centre, **kw)
+        el = time.perf_counter() - t
+        line["cpu_oracle_sampler"] = {"wall_s": round(el, 2), "n_like": o["n_like"], "logz": o["logz"],
+                                      "logz_err": o["logz_err"], "cores": oracle.num_threads(),
+                                      "lnl_evals_per_s": round(o["n_like"] / el, 1)}
+        line["speedup_wall"] = round(el / (g["wall_ms"] / 1e3), 2)
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args):
     """C3: 100 events with uneven N, rank and Q in one persistent tcgen05 launch
     replayed from a CUDA graph (launch shape chosen by the library's autotuner),
@@ -705,6 +742,8 @@ def main():
                     help="training steps of the surrogate (0: library default, 20000)")
     ap.add_argument("--kernels-only", action="store_true",
                     help="only the GPU launches of --forms (no oracle, no JSON bench line): for profilers")
+    ap.add_argument("--sampler", action="store_true",
+                    help="a nested-sampling run over the workload's likelihood (GPU driver vs CPU oracle)")
     ap.add_argument("--queries", type=int, default=0,
                     help="with --kernels-only: batch size (0: the workload's Q)")
     args = ap.parse_args()
@@ -720,6 +759,8 @@ def main():
         mf.build()
         if args.kernels_only:
             run_kernels_only(args)
+        elif args.sampler:
+            run_sampler(args)
         elif args.config == "C3":
             run_batch(args)
         else:

@@ -399,6 +399,71 @@ MF_API int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_
                               const float *held_intrinsic, const float *held_extrinsic, int n_held,
                               int E, const mf_surrogate_params *params, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Nested sampling over the online likelihood (the paper samples the
+ * posterior with nested sampling and random-walk proposals in the metric
+ * eigenbasis Delta-e: Secs. III A, III C), batched for the GPU.
+ *
+ * State of a point (dim 9, or 11 for a handle with sky-dependent patterns),
+ * with a uniform prior on the domain:
+ *   v[0..3] x in the Delta-e ball |x| <= r_ball (theta = centre + R^T x),
+ *   v[4] u in [0,1] with d_L^3 = dl_min^3 + u (dl_max^3 - dl_min^3),
+ *   v[5] cos iota in [-1,1], v[6] psi in [0,pi), v[7] phi_c in [0,2pi),
+ *   v[8] t_c in [-tc_half, tc_half], v[9] alpha in [0,2pi),
+ *   v[10] sin delta in [-1,1].
+ * Each iteration the `batch` lowest-likelihood live points die (the j-th,
+ * in ascending lnL, shrinks log X by 1/(n_live - j)); each is replaced by a
+ * surviving point moved by `walks` random-walk steps v + scale sd z (sd:
+ * per-dimension spread of the live points; z standard normal), a step being
+ * kept if it stays in the domain and its lnL exceeds the largest lnL that
+ * died.  All walkers step together: one proposal kernel, one mf_loglike call
+ * over the batch (the handle's current form), one acceptance kernel.  The
+ * scale adapts as scale *= exp(accepted fraction - 0.5) per iteration.
+ * Random numbers are the splitmix64 outputs of `seed` at counters
+ * ((iter * 65536 + walker) * 1024 + step) * 64 + slot.  Stops when the live
+ * points can add less than dlogz to log Z (or after max_iter iterations);
+ * the last live points are then added with equal shares of the remaining
+ * volume.
+ *   out_v [max_out][dim], out_lnl [max_out], out_logwt [max_out] (host):
+ *     the dead points then the final live points, in order, with their log
+ *     posterior weight lnL + log dX (unnormalised); n_samples in *res may
+ *     exceed max_out (the rest is not stored).  NULL with max_out = 0.
+ *   test_sigma > 0 selects a diagnostic likelihood with a known evidence
+ *     instead of the handle's: lnL = -|x - test_mu|^2 / (2 test_sigma^2)
+ *     (h may then be NULL: identity rotation, zero centre, dim 9).
+ * Synchronous (waits for `stream` once per iteration).  MF_E_INVAL for
+ * sizes out of range (8 <= n_live <= 65536, 1 <= batch < n_live,
+ * 1 <= walks <= 1000), MF_E_STATE for an unconfigured handle. */
+typedef struct mf_ns_params {
+    int n_live, batch, walks, max_iter;
+    double dlogz;             /* stopping threshold on the remaining log-evidence */
+    double scale0;            /* initial step scale (<= 0: 1) */
+    double r_ball;            /* intrinsic prior: Delta-e ball radius */
+    double dl_min, dl_max;    /* d_L prior range (uniform in volume), Mpc */
+    double tc_half;           /* t_c prior half-width, s */
+    unsigned long long seed;
+    double test_sigma;        /* > 0: diagnostic Gaussian likelihood */
+    double test_mu[4];
+} mf_ns_params;
+typedef struct mf_ns_result {
+    double logz, logz_err;    /* log evidence and sqrt(H / n_live) */
+    double info;              /* information H (nats) */
+    double accept, scale;     /* accepted fraction of walk steps; final scale */
+    double wall_ms;           /* wall time of the call */
+    long long n_samples;      /* dead + final live points */
+    long long n_like;         /* likelihood evaluations */
+    int iterations, converged, dim;
+} mf_ns_result;
+MF_API int mf_nested_sample(mf_handle *h, const mf_ns_params *p, mf_ns_result *res, double *out_v,
+                            double *out_lnl, double *out_logwt, int max_out, void *stream);
+
+/* Importance weights of posterior samples (Sec. III A): w_i proportional to
+ * exp(logwt_i + log_ratio_i) (log_ratio = log target prior - log sampling
+ * prior, or NULL for 1), normalised to sum 1, and the effective sample size
+ * N_eff = (sum w)^2 / sum w^2.  Host arrays of n.  MF_E_INVAL if no weight is
+ * finite. */
+MF_API int mf_reweight(const double *logwt, const double *log_ratio, int n, double *w, double *n_eff);
+
 /* Tuning / instrumentation knobs (host-side, take effect at the next call):
  *   "timing"   : 1 = record CUDA events around the main lnL kernel of each
  *                mf_loglike (read back with mf_query "kernel_ms"), 0 = off.

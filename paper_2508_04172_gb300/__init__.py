@@ -15,7 +15,7 @@ import numpy as np
 from .build import SO as _SO_PATH, build
 
 __all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch", "Mlp",
-           "svd_compress", "FORMS", "pack_node_values"]
+           "svd_compress", "FORMS", "pack_node_values", "nested_sample", "reweight"]
 
 MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
 MF_E_ILLCOND, MF_E_RANGE, MF_E_TIMEOUT, MF_E_NOTIMPL, MF_E_STATE = -4, -5, -6, -7, -8
@@ -31,6 +31,23 @@ class SurrogateParams(ctypes.Structure):
                 ("n_hidden", ctypes.c_int), ("lr", ctypes.c_float), ("lr_min", ctypes.c_float),
                 ("gate_max", ctypes.c_float), ("gate_median", ctypes.c_float),
                 ("r_gate", ctypes.c_float), ("seed", ctypes.c_ulonglong)]
+
+
+class NsParams(ctypes.Structure):
+    """mf_ns_params."""
+    _fields_ = [("n_live", ctypes.c_int), ("batch", ctypes.c_int), ("walks", ctypes.c_int),
+                ("max_iter", ctypes.c_int), ("dlogz", ctypes.c_double), ("scale0", ctypes.c_double),
+                ("r_ball", ctypes.c_double), ("dl_min", ctypes.c_double), ("dl_max", ctypes.c_double),
+                ("tc_half", ctypes.c_double), ("seed", ctypes.c_ulonglong), ("test_sigma", ctypes.c_double),
+                ("test_mu", ctypes.c_double * 4)]
+
+
+class NsResult(ctypes.Structure):
+    """mf_ns_result."""
+    _fields_ = [("logz", ctypes.c_double), ("logz_err", ctypes.c_double), ("info", ctypes.c_double),
+                ("accept", ctypes.c_double), ("scale", ctypes.c_double), ("wall_ms", ctypes.c_double),
+                ("n_samples", ctypes.c_longlong), ("n_like", ctypes.c_longlong), ("iterations", ctypes.c_int),
+                ("converged", ctypes.c_int), ("dim", ctypes.c_int)]
 
 
 class MlpTrainParams(ctypes.Structure):
@@ -98,6 +115,9 @@ def lib():
         L.mf_mlp_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
         L.mf_train_surrogate.argtypes = [vp, vp, ip, vp, vp, ip, ip, ctypes.POINTER(SurrogateParams),
                                          vp]
+        L.mf_nested_sample.argtypes = [vp, ctypes.POINTER(NsParams), ctypes.POINTER(NsResult), vp, vp, vp,
+                                       ip, vp]
+        L.mf_reweight.argtypes = [vp, vp, ip, vp, ctypes.POINTER(dp)]
         _lib = L
     return _lib
 
@@ -131,6 +151,42 @@ def svd_compress(Z: np.ndarray, rank: int, stream=None):
                                  _stream_ptr(stream) if stream is not None else None),
            "mf_svd_compress")
     return coef, basis, sv
+
+
+def nested_sample(model, n_live=1000, batch=100, walks=150, dlogz=0.1, max_iter=100000, r_ball=0.9,
+                  dl_range=(100.0, 400.0), tc_half=5e-3, seed=0, scale0=1.0, test_sigma=0.0,
+                  test_mu=(0.0, 0.0, 0.0, 0.0), max_out=None, stream=None):
+    """mf_nested_sample on an Interpolant (or None with test_sigma > 0).
+    Returns a dict: the result fields plus 'v' [n, dim] (states), 'lnl' [n],
+    'logwt' [n] of the dead then final live points."""
+    p = NsParams(int(n_live), int(batch), int(walks), int(max_iter), float(dlogz), float(scale0), float(r_ball),
+                 float(dl_range[0]), float(dl_range[1]), float(tc_half), int(seed), float(test_sigma),
+                 (ctypes.c_double * 4)(*[float(v) for v in test_mu]))
+    r = NsResult()
+    dim = 11 if (model is not None and getattr(model, "sky", False)) else 9
+    if max_out is None:
+        max_out = int(n_live) * 200
+    v = np.zeros((max_out, dim))
+    lnl = np.zeros(max_out)
+    lw = np.zeros(max_out)
+    _check(lib().mf_nested_sample(None if model is None else model._h, ctypes.byref(p), ctypes.byref(r),
+                                  _ptr(v), _ptr(lnl), _ptr(lw), int(max_out),
+                                  _stream_ptr(stream)), "mf_nested_sample")
+    out = {k: getattr(r, k) for k, _ in NsResult._fields_}
+    n = min(int(r.n_samples), max_out)
+    out.update(v=v[:n, :r.dim], lnl=lnl[:n], logwt=lw[:n])
+    return out
+
+
+def reweight(logwt, log_ratio=None):
+    """mf_reweight: normalised importance weights and N_eff."""
+    lw = np.ascontiguousarray(logwt, dtype=np.float64)
+    lr = None if log_ratio is None else np.ascontiguousarray(log_ratio, dtype=np.float64)
+    w = np.empty_like(lw)
+    ne = ctypes.c_double()
+    _check(lib().mf_reweight(_ptr(lw), None if lr is None else _ptr(lr), lw.shape[0], _ptr(w), ctypes.byref(ne)),
+           "mf_reweight")
+    return w, ne.value
 
 
 def pack_node_values(coef: np.ndarray, sigma: np.ndarray) -> np.ndarray:
@@ -209,6 +265,7 @@ class Interpolant:
     def set_detectors(self, det, d_ref):
         d = np.ascontiguousarray(det, dtype=np.float64)
         _check(lib().mf_set_detectors(self._h, _ptr(d), float(d_ref)), "mf_set_detectors")
+        self.sky = False
 
     def set_sky(self, tensor, pos, tau, gmst0, omega, d_ref):
         """mf_set_sky: tensor [n_det,3,3], pos [n_det,3] (seconds), tau [n_det]
@@ -219,6 +276,7 @@ class Interpolant:
         t = None if tau is None else np.ascontiguousarray(tau, dtype=np.float64)
         _check(lib().mf_set_sky(self._h, _ptr(T), _ptr(P), None if t is None else _ptr(t), float(gmst0),
                                 float(omega), float(d_ref)), "mf_set_sky")
+        self.sky = True
 
     def set_rotation(self, metric=None, centre=None):
         m = None if metric is None else np.ascontiguousarray(metric, dtype=np.float64)

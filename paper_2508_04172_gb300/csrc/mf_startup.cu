@@ -462,6 +462,9 @@ int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
         if (rc) return rc;
         normalize64<<<1, 256, 0, st>>>(y.p, N, x.p, nrm.p);
     }
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaMemcpyAsync(&inv, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+
     // solve Phi X = [F | P]
     assemble_rhs<<<dim3((N + 255) / 256, ncols), 256, 0, st>>>(F.p, h->d_nodes64, N, K, P, B.p);
     MF_CUDA(cudaGetLastError());
