@@ -179,6 +179,14 @@ MF_API int mf_set_sky(mf_handle *h, const double *tensor, const double *pos, con
  */
 MF_API int mf_set_rotation(mf_handle *h, const double *metric, const double *centre);
 
+/*
+ * General affine frame instead of mf_set_rotation: x = A (theta - centre)
+ * with A host [4][4] row-major (any invertible map, e.g. the rotation into
+ * the metric eigenbasis followed by a division by the ellipsoid's semi-axes,
+ * which is what mf_place_nodes returns), centre host [4] or NULL.
+ */
+MF_API int mf_set_frame(mf_handle *h, const double *A, const double *centre);
+
 /* Select the Phi.W arithmetic (default MF_FORM_FP32).  Converts the weights
  * for the form on first use (synchronous on the legacy stream). */
 MF_API int mf_set_form(mf_handle *h, mf_form form);
@@ -398,6 +406,62 @@ typedef struct mf_surrogate_params {
 MF_API int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train,
                               const float *held_intrinsic, const float *held_extrinsic, int n_held,
                               int E, const mf_surrogate_params *params, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Start-up generation (Sec. II C) from data, on the GPU.
+ *
+ * Frequency-domain stand-in templates (no waveform model of the paper is
+ * available here): mode (l, m) at intrinsic point theta, with F = 2 f / m,
+ *   h_{l,-m}(f) = amp (F/f_ref)^(-7/6) exp(-i (m/2) sum_a s_a theta_a u_a(F/f_ref))
+ * for F_lo(theta) <= F <= f_hi, F_lo = f_lo exp(cut_rate cut_dir . theta),
+ * u_a(x) = x^p_a - 1 - p_a (x - 1); 0 elsewhere.  One-sided frequency grid
+ * f_j = j / (L dt), j = 0 .. L/2. */
+typedef struct mf_wave {
+    int n_modes;
+    int ell_m[5][2];
+    double amp[5];
+    double f_lo, f_hi, f_ref;
+    double powers[4], scales[4];
+    double cut_dir[4], cut_rate;
+    int L;                    /* FFT length: power of two, 16 .. 8192 */
+    double dt;                /* sample spacing of the overlap series (s) */
+} mf_wave;
+
+/* Node placement (Sec. II C 1): the constant-match ellipsoid
+ * x^T g x <= mismatch of the metric g (host [4][4], SPD; Eq. MisMatch),
+ * semi-axes a_d = sqrt(mismatch / lambda_d) along the eigenvectors (ascending
+ * eigenvalue, rows of R as in mf_set_rotation), the longest (d = 0) times
+ * `squeeze` in (0, 1]; nodes theta_n = centre + R^T (a * y_n) with y_n the
+ * first N points of the 4-D Halton sequence (bases 2, 3, 5, 7; indices
+ * skip+1, skip+2, ...) mapped to [-1,1]^4 that fall in the unit ball,
+ * selected in index order on the GPU.
+ *   theta : host out [N][4] (sampler frame);  y : host out [N][4] or NULL
+ *   (whitened nodes, the unit ball);  frame : host out [4][4] or NULL,
+ *   A = diag(1/a) R, so that y = A (theta - centre) (for mf_set_frame). */
+MF_API int mf_place_nodes(const double *metric, const double *centre, double mismatch, double squeeze, int N,
+                          long long skip, double *theta, double *y, double *frame);
+
+/* Squeeze factor (Sec. II C 1): the true match (Eq. Match: normalised
+ * overlap of the dominant-mode templates, modulus, maximised over the L
+ * circular time shifts) from the centre to centre + t a_0 e_0 along the
+ * longest axis, t = i / n_t (i = 1..n_t), each point one CTA with an
+ * inverse FFT; *kappa = the first t where it falls below 1 - mismatch
+ * (linear interpolation; 1 if it never does).  psd host [L/2+1];
+ * match_out host [n_t] or NULL.  Synchronous. */
+MF_API int mf_squeeze_factor(const mf_wave *w, const double *psd, const double *metric, const double *centre,
+                             double mismatch, int n_t, double *kappa, double *match_out);
+
+/* Node overlaps (Sec. II C 2) of N nodes against n_det detectors' data:
+ *   z[k][mu][n][s] = 4 df sum_j conj(h_mu(f_j; theta_n)) d_k(f_j) / S_k(f_j)
+ *                    exp(2 pi i f_j t_s),  t_s = (s - M/2) dt, s = 0..M-1
+ * (the circular time shifts of an inverse FFT of length L, FP64, one CTA per
+ * (node, mode)), and the cross terms
+ *   sigma[k][n][mu][nu] = 4 df sum_j conj(h_mu) h_nu / S_k   (Hermitian).
+ *   theta : host [N][4];  data : host [n_det][L/2+1][2] (re, im);
+ *   psd : host [n_det][L/2+1];  z : host out [n_det][n_modes][N][M][2];
+ *   sigma : host out [n_det][N][n_modes][n_modes][2].  Synchronous. */
+MF_API int mf_standin_overlaps(const mf_wave *w, const double *theta, int N, const double *data,
+                               const double *psd, int n_det, int M, double *z, double *sigma, void *stream);
 
 /* ------------------------------------------------------------------------
  * Nested sampling over the online likelihood (the paper samples the

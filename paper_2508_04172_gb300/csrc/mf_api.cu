@@ -93,51 +93,70 @@ static int split_exact(const std::vector<int> &w, int count, std::vector<int> &s
 }
 
 // Device column layout: per detector, its overlap groups (interleaved Re/Im
-// of the rank coefficients, padded to 8) then its cross-term group; groups
-// are packed into passes of at most pass_max columns (each padded to 16).
+// of a run of SVD coefficients, padded to 8 columns) then its cross-term
+// group, packed contiguously into passes of at most pass_max columns (each
+// padded to 16).  The layout takes the fewest passes that fit (or exactly
+// pass_count), balanced by a min-max split; when a mode's coefficients do
+// not pack into that many passes as whole groups, every mode is split into
+// 2, 4, ... runs of coefficients (lnL is linear in each coefficient, so a
+// mode's contribution may be summed over passes).
 int build_layout(mf_handle *h) {
     const int nd = h->n_det, nm = h->n_modes, l = h->rank;
     auto up = [](int x, int a) { return (x + a - 1) / a * a; };
-    struct G { int kind, det, mode, width; };
+    struct G { int kind, det, mode, width, i0, ni; };
+    auto make = [&](int nsplit) {
+        std::vector<G> gs;
+        const int chunk = ((l + nsplit - 1) / nsplit + 3) / 4 * 4;   // coefficients per run (a multiple of 4)
+        for (int k = 0; k < nd; ++k) {
+            for (int mu = 0; mu < nm; ++mu)
+                for (int i0 = 0; i0 < l; i0 += chunk) {
+                    const int ni = std::min(chunk, l - i0);
+                    gs.push_back({0, k, mu, up(2 * ni, kGroupAlign), i0, ni});
+                }
+            gs.push_back({1, k, 0, up(nm * nm, kGroupAlign), 0, 0});
+        }
+        return gs;
+    };
+    const int pmax = h->pass_max;
     std::vector<G> gs;
-    for (int k = 0; k < nd; ++k) {
-        for (int mu = 0; mu < nm; ++mu) gs.push_back({0, k, mu, up(2 * l, kGroupAlign)});
-        gs.push_back({1, k, 0, up(nm * nm, kGroupAlign)});
-    }
-    if ((int)gs.size() > kMaxGroups) return MF_E_INVAL;
-    int total = 0, gmax = 0;
-    for (auto &g : gs) { total += g.width; gmax = std::max(gmax, g.width); }
-    const int pmax = std::max(h->pass_max, up(gmax, kPassAlign));
-    const int npass_min = (total + pmax - 1) / pmax;
-    const int target = (total + npass_min - 1) / npass_min;
-    // exact pass count requested: contiguous min-max split of the groups
     std::vector<int> cut_at;
-    if (h->pass_count > 0) {
-        std::vector<int> w;
-        for (auto &g : gs) w.push_back(g.width);
-        int widest = split_exact(w, h->pass_count, cut_at);
-        if (widest < 0 || widest > pmax) return MF_E_INVAL;
+    bool found = false;
+    for (int npass = 1; npass <= kMaxPass && !found; ++npass) {
+        if (h->pass_count > 0 && npass != h->pass_count) continue;
+        for (int nsplit = 1; nsplit <= 32 && !found; nsplit *= 2) {
+            std::vector<G> cand = make(nsplit);
+            if ((int)cand.size() > kMaxGroups) break;
+            int total = 0, gmax = 0;
+            for (auto &g : cand) { total += g.width; gmax = std::max(gmax, g.width); }
+            if (up(gmax, kPassAlign) > pmax) continue;       // a finer split may fit
+            if (npass * pmax < total || npass > (int)cand.size()) break;
+            std::vector<int> w;
+            for (auto &g : cand) w.push_back(g.width);
+            std::vector<int> start;
+            const int widest = split_exact(w, npass, start);
+            if (widest > 0 && widest <= pmax) {
+                gs = cand;
+                cut_at = start;
+                found = true;
+            }
+        }
     }
+    if (!found) return MF_E_INVAL;
     h->groups.clear();
     h->passes.clear();
     Pass cur{0, 0, 0, 0};
     int col = 0;
     size_t next_cut = 1;
     for (size_t i = 0; i < gs.size(); ++i) {
-        bool split;
-        if (!cut_at.empty()) {
-            split = next_cut < cut_at.size() && (int)i == cut_at[next_cut];
-            if (split) ++next_cut;
-        } else {
-            split = cur.ng > 0 && (cur.width + gs[i].width > pmax || cur.width >= target);
-        }
+        const bool split = next_cut < cut_at.size() && (int)i == cut_at[next_cut];
         if (split) {
+            ++next_cut;
             cur.width = up(cur.width, kPassAlign);
             h->passes.push_back(cur);
             col += cur.width;
             cur = Pass{col, 0, (int)h->groups.size(), 0};
         }
-        Group g{gs[i].kind, gs[i].det, gs[i].mode, cur.width, gs[i].width};
+        Group g{gs[i].kind, gs[i].det, gs[i].mode, cur.width, gs[i].width, gs[i].i0, gs[i].ni};
         h->groups.push_back(g);
         cur.width += gs[i].width;
         cur.ng++;
@@ -157,9 +176,9 @@ int build_layout(mf_handle *h) {
             int base = ps.col0 + g.col;
             if (g.kind == 0) {
                 int ucol = (g.det * nm + g.mode) * 2 * l;
-                for (int i = 0; i < l; ++i) {
-                    h->user_of_dev[base + 2 * i] = ucol + i;
-                    h->user_of_dev[base + 2 * i + 1] = ucol + l + i;
+                for (int i = 0; i < g.ni; ++i) {
+                    h->user_of_dev[base + 2 * i] = ucol + g.i0 + i;
+                    h->user_of_dev[base + 2 * i + 1] = ucol + l + g.i0 + i;
                 }
             } else {
                 int ucol = sig0 + g.det * nm * nm;
@@ -448,6 +467,16 @@ int mf_set_rotation(mf_handle *h, const double *metric, const double *centre) {
     } else {
         for (int i = 0; i < 16; ++i) h->R[i] = (i % 5 == 0) ? 1.0 : 0.0;
     }
+    for (int i = 0; i < 4; ++i) h->centre[i] = centre ? centre[i] : 0.0;
+    ++h->gen;
+    return MF_OK;
+}
+
+int mf_set_frame(mf_handle *h, const double *A, const double *centre) {
+    if (!h || !A) return MF_E_INVAL;
+    for (int i = 0; i < 16; ++i)
+        if (!std::isfinite(A[i])) return MF_E_INVAL;
+    memcpy(h->R, A, sizeof(h->R));
     for (int i = 0; i < 4; ++i) h->centre[i] = centre ? centre[i] : 0.0;
     ++h->gen;
     return MF_OK;

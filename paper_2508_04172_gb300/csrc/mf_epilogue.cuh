@@ -183,21 +183,23 @@ __device__ __forceinline__ float pass_lnl(const EpiParams &P, const Pass &ps, co
         if (G.kind == 0) {
             // Eq. (SVD) at t_c + dt_k: z = sum_i C_i S_i(u), S_i the spline of
             // basis vector i on interval j (cubic in u from the table)
-            const float4 *tp = P.cubic + ((size_t)(G.det * P.n_modes + G.mode) * P.M + j) * P.rank * 2;
+            // this group's coefficients [G.i0, G.i0 + G.ni) of the mode
+            const float4 *tp = P.cubic + (((size_t)(G.det * P.n_modes + G.mode) * P.M + j) * P.rank + G.i0) * 2;
+            const int ni = G.ni;
             float zr = 0.f, zi = 0.f;
             // table entries of the next 4 coefficients are loaded one chunk
             // ahead so their latency overlaps the current chunk's math
             float4 cur[8], nxt[8];
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                const bool in = t < P.rank;
+                const bool in = t < ni;
                 cur[2 * t] = in ? ldg_stream(tp + 2 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
                 cur[2 * t + 1] = in ? ldg_stream(tp + 2 * t + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            for (int i0 = 0; i0 < P.rank; i0 += 4) {
+            for (int i0 = 0; i0 < ni; i0 += 4) {
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const bool in = i0 + 4 + t < P.rank;
+                    const bool in = i0 + 4 + t < ni;
                     nxt[2 * t] = in ? ldg_stream(tp + 2 * (i0 + 4 + t)) : make_float4(0.f, 0.f, 0.f, 0.f);
                     nxt[2 * t + 1] = in ? ldg_stream(tp + 2 * (i0 + 4 + t) + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }

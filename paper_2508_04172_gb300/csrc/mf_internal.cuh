@@ -24,15 +24,17 @@ constexpr int kGroupAlign = 8;        // every column group padded to 8 columns
 constexpr int kPassAlign = 16;        // pass width multiple of 16 (MMA N granularity)
 
 // One column group of the device layout: a detector/mode overlap block
-// (interleaved Re/Im of `rank` SVD coefficients) or a detector's cross-term
-// block (n_modes diagonals then interleaved Re/Im of the strict upper
-// triangle).
+// (interleaved Re/Im of a run of its SVD coefficients) or a detector's
+// cross-term block (n_modes diagonals then interleaved Re/Im of the strict
+// upper triangle).
 struct Group {
     int kind;     // 0 = overlap z_k,mu ; 1 = cross terms sigma_k
     int det;
     int mode;     // overlap groups only
     int col;      // first device column of the group, relative to its pass
     int width;    // padded width (multiple of kGroupAlign)
+    int i0, ni;   // overlap groups: SVD coefficients [i0, i0 + ni) of the mode (a mode
+                  // may be split over several groups; lnL is linear in each coefficient)
 };
 
 struct Pass {
@@ -207,6 +209,7 @@ int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBat
                     cudaStream_t st);
 bool is_tc_form(mf_form f);
 // surrogate network (MF_FORM_MLP)
+int metric_eig(const double *metric, double *R_out);   // rows = eigenvectors, ascending
 int surrogate_prepare(mf_handle *h);
 void free_surrogate(mf_handle *h);
 int loglike_surrogate(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,

@@ -88,6 +88,17 @@ struct BatchSrc {
 // Work item handled by cluster `cid` in round r: snake order (forward in
 // even rounds, backward in odd ones), so that with items sorted by
 // decreasing cost the clusters' totals stay close.
+//
+// Node-block order of a tile: the k-loop of tile t starts at block
+// rot = 11 t mod nkb and wraps around, so that the clusters (which start
+// together) do not all fetch the same weight tile at the same time.  The
+// order depends only on the tile, so a query's sum is formed in the same
+// order whatever the launch shape.
+__device__ __forceinline__ int tile_rot(int tile, int nkb) { return (int)(((long long)tile * 11) % nkb); }
+__device__ __forceinline__ int rot_kb(int kb, int rot, int nkb) {
+    const int k = kb + rot;
+    return k >= nkb ? k - nkb : k;
+}
 __device__ __forceinline__ int item_of(int r, int cid, int nc) {
     return r * nc + ((r & 1) ? nc - 1 - cid : cid);
 }
@@ -111,7 +122,7 @@ __device__ __forceinline__ void rotate_row(const RotParams &rot, const float *in
 // (kb = rank, rank + np, ...) of its cluster's work items, in order.
 struct NodeCursor {
     int r;                  // round of the current work item
-    int kb, nkb;
+    int kb, nkb, rot;
     const float4 *nodes;
     bool valid;             // false past the cluster's last work item
 };
@@ -129,6 +140,7 @@ __device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, in
         src.item(it, e, tile);
         const TcEvent &ev = src.event(e);
         cu.nkb = ev.nkb;
+        cu.rot = tile_rot(tile, ev.nkb);
         cu.nodes = ev.nodes_s;
         cu.kb = rank;
     }
@@ -241,11 +253,13 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                 const int col0 = ev.epi.passes[rank].col0;
                 const uint32_t bytes = (uint32_t)(NB * ev.nbox * kRowBytes);
                 const int nkb = ev.nkb;
+                const int rot = tile_rot(tile, nkb);
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(emptyB + s, ph ^ 1, err, 1, kb)) { ok = false; break; }
                     mbar_expect_tx(fullB + s, bytes);
-                    tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kb * kKB, col0, fullB + s);
-                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kb * kKB, col0, fullB + s);
+                    const int kx = rot_kb(kb, rot, nkb) * kKB;
+                    tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kx, col0, fullB + s);
+                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kx, col0, fullB + s);
                     ++issued;
                     if (++s == SB) { s = 0; ph ^= 1; }
                 }
@@ -328,11 +342,12 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
         bool ok = true;
         // this lane's node of the next kNodeAhead node blocks of this CTA (FIFO)
         float4 yq[kNodeAhead];
-        NodeCursor cu{-1, 0, 0, nullptr, true};
+        NodeCursor cu{-1, 0, 0, 0, nullptr, true};
         cursor_settle(cu, src, cid, nc, rank);
 #pragma unroll
         for (int dd = 0; dd < kNodeAhead; ++dd) {
-            yq[dd] = cu.valid ? ldg_keep(cu.nodes + cu.kb * kKB + nperm) : make_float4(0.f, 0.f, 0.f, 0.f);
+            yq[dd] = cu.valid ? ldg_keep(cu.nodes + rot_kb(cu.kb, cu.rot, cu.nkb) * kKB + nperm)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
             cu.kb += np;
             cursor_settle(cu, src, cid, nc, rank);
         }
@@ -344,6 +359,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
             const TcEvent &ev = src.event(e);
             const EvIO io = src.io(e);
             const int N = ev.N, P = ev.P, nkb = ev.nkb;
+            const int rot = tile_rot(tile, nkb);
             float2 X[RPT / 2][4];   // row pairs (rg + 2h RS, rg + (2h+1) RS), per coordinate
             float4 xu[RPT];
             {
@@ -368,17 +384,18 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                 const float4 ycur = yq[0];
 #pragma unroll
                 for (int dd = 0; dd < kNodeAhead - 1; ++dd) yq[dd] = yq[dd + 1];
-                yq[kNodeAhead - 1] =
-                    cu.valid ? ldg_keep(cu.nodes + cu.kb * kKB + nperm) : make_float4(0.f, 0.f, 0.f, 0.f);
+                yq[kNodeAhead - 1] = cu.valid ? ldg_keep(cu.nodes + rot_kb(cu.kb, cu.rot, cu.nkb) * kKB + nperm)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
                 cu.kb += np;
                 cursor_settle(cu, src, cid, nc, rank);
                 float4 *scr = sN + ((warp - 2) * 2 + sbuf) * kKB;
                 sbuf ^= 1;
                 scr[lane] = ycur;
                 __syncwarp();
-                const int n0 = kb * kKB + c * 8;
+                const int kd = rot_kb(kb, rot, nkb);   // node block held by this k-step
+                const int n0 = kd * kKB + c * 8;
                 float v[RPT][8];   // rows rg + RS j, nodes n0 .. n0+7
-                const bool full = (kb * kKB + kKB <= N);
+                const bool full = (kd * kKB + kKB <= N);
 #pragma unroll
                 for (int e8 = 0; e8 < 8; ++e8) {
                     const int n = n0 + e8;

@@ -77,6 +77,10 @@ struct Tc2Call {
 
 // COLS = true: columns-only variant (mf_eval_columns), the epilogue writes
 // each pass's interpolated columns instead of combining them into lnL.
+// Node-block order of tile t: starts at 11 t mod nkb and wraps (the same
+// order as the cluster design, so the two give bitwise equal sums).
+__device__ __forceinline__ int tile_rot2(int tile, int nkb) { return (int)(((long long)tile * 11) % nkb); }
+
 template <int NM, int AT, int TERMS, bool COLS = false>
 __global__ void __launch_bounds__(kThreads2, 1)
 tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c) {
@@ -135,11 +139,13 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
             bool ok = true;
             for (int it = blockIdx.x; it < c.n_items && ok; it += c.n_ctas) {
                 const int col0 = ev.epi.passes[it % c.n_pass].col0;
+                const int rot = tile_rot2(it / c.n_pass, nkb);
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(emptyB + s, ph ^ 1, err, 1, kb)) { ok = false; break; }
                     mbar_expect_tx(fullB + s, bytes);
-                    tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kb * kKB, col0, fullB + s);
-                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kb * kKB, col0, fullB + s);
+                    const int kx = (kb + rot < nkb ? kb + rot : kb + rot - nkb) * kKB;
+                    tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kx, col0, fullB + s);
+                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kx, col0, fullB + s);
                     ++issued;
                     if (++s == SB) { s = 0; ph ^= 1; }
                 }
@@ -206,7 +212,11 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
         int nit = blockIdx.x, nkb_f = 0;
         float4 ynext = make_float4(0.f, 0.f, 0.f, 0.f);
         auto fetch = [&]() {
-            if (nit < c.n_items && lane < 16) ynext = ldg_keep(ev.nodes_s + nkb_f * kKB + 16 * h + lane);
+            if (nit < c.n_items && lane < 16) {
+                const int r = tile_rot2(nit / c.n_pass, nkb);
+                const int kd = nkb_f + r < nkb ? nkb_f + r : nkb_f + r - nkb;
+                ynext = ldg_keep(ev.nodes_s + kd * kKB + 16 * h + lane);
+            }
             if (++nkb_f == nkb) { nkb_f = 0; nit += c.n_ctas; }
         };
         fetch();
@@ -226,13 +236,14 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
             const float pre = ev.rot.pre;
             const float2 X0 = make_float2(x[0] * pre, x[0] * pre), X1 = make_float2(x[1] * pre, x[1] * pre);
             const float2 X2 = make_float2(x[2] * pre, x[2] * pre), X3 = make_float2(x[3] * pre, x[3] * pre);
+            const int rot = tile_rot2(tile, nkb);
             for (int kb = 0; kb < nkb; ++kb) {
                 float4 *buf = scr + sbuf * 16;
                 sbuf ^= 1;
                 if (lane < 16) buf[lane] = ynext;
                 fetch();
                 __syncwarp();
-                const int n0 = kb * kKB + 16 * h;
+                const int n0 = (kb + rot < nkb ? kb + rot : kb + rot - nkb) * kKB + 16 * h;
                 float v[16];
                 if (n0 + 16 <= ev.N) {
 #pragma unroll

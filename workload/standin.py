@@ -313,3 +313,140 @@ def make_queries(ev: Event, Q: int, seed: int | None = None, radius: float = 0.9
         ext[:, 5] = rng.uniform(0.0, 2 * np.pi, Q)
         ext[:, 6] = np.arcsin(rng.uniform(-1.0, 1.0, Q))
     return theta.astype(np.float32), ext.astype(np.float32)
+
+
+# ----------------------------------------------------------------------------
+# Frequency-domain stand-in for the start-up stage (node placement and node
+# overlaps from data).  Inputs only: a mode waveform model, a PSD shape,
+# synthetic detector data (an injection plus Gaussian noise) and the model's
+# metric at the ellipsoid centre.  The start-up arithmetic itself (Halton
+# placement, squeezing, FFT overlaps, SVD, RBF fit) lives in ``oracle/`` and
+# in the CUDA library.
+#
+# Mode (l, m) at intrinsic point theta (sampler frame), one-sided frequency f:
+#   F = 2 f / m (the frequency of the dominant harmonic emitted at the same
+#   time), nonzero for F_lo(theta) <= F <= f_hi with the lower band edge
+#   F_lo(theta) = f_lo exp(c_r (c_v . theta)) (the match then falls off
+#   faster than the quadratic metric predicts far from the centre),
+#   h_{l,-m}(f) = amp_lm (F / f_ref)^(-7/6) exp(-i (m/2) Psi(F; theta)),
+#   Psi(F; theta) = sum_a s_a theta_a u_a(F / f_ref),
+#   u_a(x) = x^p_a - 1 - p_a (x - 1)   (value and slope removed at f_ref),
+#   with p = (-5/3, -2/3, 1/3, 5/3): frequency powers like those of a
+#   post-Newtonian phase, one per intrinsic coordinate.
+# PSD: S(f) = (f / f_ref)^-4 + 2 + 2 (f / f_ref)^2 (arbitrary units).
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass(frozen=True)
+class WaveSpec:
+    modes: tuple = HM4
+    f_lo: float = 30.0
+    f_hi: float = 1000.0
+    f_ref: float = 100.0
+    powers: tuple = (-5.0 / 3.0, -2.0 / 3.0, 1.0 / 3.0, 5.0 / 3.0)
+    scales: tuple = (20.0, 20.0, 20.0, 20.0)     # rad per unit theta_a
+    cut_dir: tuple = (0.0, 0.0, 0.0, 0.0)        # c_v
+    cut_rate: float = 0.0                        # c_r
+    L: int = 8192                                # FFT length (df = 1 / (L dt))
+    dt: float = 1.0 / 4096.0
+
+    @property
+    def df(self) -> float:
+        return 1.0 / (self.L * self.dt)
+
+    def freqs(self) -> np.ndarray:
+        return np.arange(self.L // 2 + 1) * self.df
+
+
+def standin_psd(ws: WaveSpec) -> np.ndarray:
+    """PSD on the one-sided grid (bin 0 set to the bin-1 value)."""
+    f = ws.freqs().copy()
+    f[0] = f[1]
+    x = f / ws.f_ref
+    return x ** -4 + 2.0 + 2.0 * x ** 2
+
+
+def injection_modes(ws: WaveSpec, theta) -> np.ndarray:
+    """h_{l,-m}(f) of every mode at one point theta [4]: [n_modes, L/2+1] complex."""
+    f = ws.freqs()
+    out = np.zeros((len(ws.modes), f.size), complex)
+    f_lo = ws.f_lo * np.exp(ws.cut_rate * float(np.dot(ws.cut_dir, theta)))
+    for j, (ell, m) in enumerate(ws.modes):
+        F = 2.0 * f / m
+        x = F / ws.f_ref
+        inb = (F >= f_lo) & (F <= ws.f_hi)
+        xs = np.where(inb, x, 1.0)
+        psi = np.zeros_like(xs)
+        for a in range(4):
+            p = ws.powers[a]
+            psi += ws.scales[a] * theta[a] * (xs ** p - 1.0 - p * (xs - 1.0))
+        amp = AMP[(ell, m)] * xs ** (-7.0 / 6.0)
+        out[j] = np.where(inb, amp * np.exp(-1j * 0.5 * m * psi), 0.0)
+    return out
+
+
+@dataclasses.dataclass
+class StartupEvent:
+    ws: WaveSpec
+    psd: np.ndarray            # [n_det, L/2+1]
+    data: np.ndarray           # [n_det, L/2+1] complex: injection + noise
+    theta_inj: np.ndarray      # [4]
+    centre: np.ndarray         # [4] ellipsoid centre
+    metric: np.ndarray         # [4, 4] model metric at the centre (22 mode)
+    det: np.ndarray            # [n_det, 3] frozen patterns and delays
+    mismatch: float            # 1 - match of the ellipsoid
+
+
+def model_metric(ws: WaveSpec, psd: np.ndarray) -> np.ndarray:
+    """Metric of the 22 mode's match at any point (the phase is linear in
+    theta): g_ab = 1/2 [<d_a Psi d_b Psi> minus its projection on time and
+    phase shifts], <.> the |h|^2 / S weighted mean over frequency."""
+    f = ws.freqs()
+    x = np.where(f > 0, f / ws.f_ref, 1.0)
+    inb = (f >= ws.f_lo) & (f <= ws.f_hi)
+    w = np.where(inb, x ** (-7.0 / 3.0) / psd, 0.0)
+    w /= w.sum()
+    D = np.stack([ws.scales[a] * (x ** p - 1.0 - p * (x - 1.0)) for a, p in enumerate(ws.powers)] +
+                 [2 * np.pi * f, np.ones_like(f)])          # derivatives wrt theta, t, phi
+    G = (D[:, None, :] * D[None, :, :] * w[None, None, :]).sum(-1)
+    Gtt = G[4:, 4:]
+    g = G[:4, :4] - G[:4, 4:] @ np.linalg.solve(Gtt, G[4:, :4])
+    return 0.5 * (g + g.T) * 0.5
+
+
+def make_startup_event(n_det: int = 3, seed: int = 7000, snr: float = 20.0, mismatch: float = 0.05,
+                       ws: WaveSpec | None = None) -> StartupEvent:
+    """Synthetic detector data for the start-up: an injection of every mode
+    (seeded complex mode amplitudes standing in for the extrinsic factors,
+    scaled to the network SNR `snr`, seeded delays) plus Gaussian noise with
+    the stand-in PSD; the ellipsoid is centred on the injection."""
+    ws = ws or WaveSpec()
+    rng = np.random.default_rng(seed)
+    psd1 = standin_psd(ws)
+    if ws.cut_rate == 0.0:
+        # the band edge moves along the metric's longest axis (1.2 e-folds
+        # over its half-length at the ellipsoid's match)
+        lam, vec = np.linalg.eigh(model_metric(ws, psd1))
+        a0 = np.sqrt(mismatch / lam[0])
+        ws = dataclasses.replace(ws, cut_dir=tuple(float(v) for v in vec[:, 0]), cut_rate=1.2 / a0)
+    psd = np.stack([psd1 * rng.uniform(0.8, 1.25) for _ in range(n_det)])
+    theta_inj = rng.uniform(-0.2, 0.2, 4)
+    h = injection_modes(ws, theta_inj)
+    f = ws.freqs()
+    det = np.empty((n_det, 3))
+    data = np.zeros((n_det, f.size), complex)
+    for k in range(n_det):
+        amp = np.sin(np.pi / 3) if n_det == 1 else rng.uniform(0.3, 1.0)
+        chi = rng.uniform(0, np.pi)
+        dt_k = 0.0 if n_det == 1 else rng.uniform(-0.021, 0.021)
+        det[k] = (amp * np.cos(2 * chi), amp * np.sin(2 * chi), dt_k)
+        c = rng.normal(size=len(ws.modes)) + 1j * rng.normal(size=len(ws.modes))
+        data[k] = (c[:, None] * h).sum(0) * np.exp(-2j * np.pi * f * dt_k)
+    # scale the signal to the requested network SNR, then add noise
+    rho2 = sum(4 * ws.df * np.sum(np.abs(data[k]) ** 2 / psd[k]) for k in range(n_det))
+    data *= snr / np.sqrt(rho2)
+    for k in range(n_det):
+        sd = np.sqrt(psd[k] / (4 * ws.df))
+        data[k] += sd * (rng.normal(size=f.size) + 1j * rng.normal(size=f.size))
+        data[k, 0] = 0.0
+    metric = model_metric(ws, psd[0])
+    return StartupEvent(ws, psd, data, theta_inj, theta_inj.copy(), metric, det, mismatch)
