@@ -180,7 +180,7 @@ class Model:
     overlaps: per-(det, mode) SVD, one RBF fit for all columns, rotation."""
 
     def __init__(self, nodes, Z, sigma, rank, eps, tail_degree, modes, det, t0, dt,
-                 d_ref, metric=None, centre=None, stencil=10, sky=None):
+                 d_ref, metric=None, centre=None, stencil=10, sky=None, frame=None):
         nd, nm, N, M = Z.shape
         self.nodes = np.ascontiguousarray(nodes, dtype=np.float64)
         self.rank, self.eps, self.tail_degree = rank, float(eps), tail_degree
@@ -198,7 +198,9 @@ class Model:
         self.basis = np.ascontiguousarray(np.stack([B.real, B.imag], axis=-1))
         self.det = np.ascontiguousarray(det, dtype=np.float64)
         self.t0, self.dt, self.d_ref = float(t0), float(dt), float(d_ref)
-        self.R = np.ascontiguousarray(metric_rotation(metric))
+        # x = R (theta - c): the metric eigenbasis, or a given affine frame
+        self.R = np.ascontiguousarray(metric_rotation(metric) if frame is None else
+                                      np.asarray(frame, dtype=np.float64))
         self.centre = np.ascontiguousarray(np.zeros(4) if centre is None else centre,
                                            dtype=np.float64)
         self.ell_m = np.ascontiguousarray(np.array(self.modes, dtype=np.int32).reshape(-1))

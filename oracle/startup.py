@@ -72,18 +72,16 @@ def template(ws, theta) -> np.ndarray:
     nf = ws.L // 2 + 1
     out = np.zeros((len(ws.modes), nf), complex)
     f_lo = ws.f_lo * math.exp(ws.cut_rate * sum(ws.cut_dir[a] * theta[a] for a in range(4)))
+    f = np.arange(nf) * ws.df
     for j, (ell, m) in enumerate(ws.modes):
-        for i in range(nf):
-            F = 2.0 * i * ws.df / m
-            if F < f_lo or F > ws.f_hi:
-                continue
-            x = F / ws.f_ref
-            psi = 0.0
-            for a in range(4):
-                p = ws.powers[a]
-                psi += ws.scales[a] * theta[a] * (x ** p - 1.0 - p * (x - 1.0))
-            out[j, i] = AMP[(ell, m)] * x ** (-7.0 / 6.0) * complex(math.cos(-0.5 * m * psi),
-                                                                    math.sin(-0.5 * m * psi))
+        F = 2.0 * f / m
+        keep = (F >= f_lo) & (F <= ws.f_hi) & (F > 0)
+        x = F[keep] / ws.f_ref
+        psi = np.zeros_like(x)
+        for a in range(4):
+            p = ws.powers[a]
+            psi += ws.scales[a] * theta[a] * (x ** p - 1.0 - p * (x - 1.0))
+        out[j, keep] = AMP[(ell, m)] * x ** (-7.0 / 6.0) * np.exp(-0.5j * m * psi)
     return out
 
 
@@ -138,3 +136,17 @@ def squeeze_factor(ws, psd, metric, centre, mismatch: float, n_t: int = 64) -> f
             return prev_t + (t - prev_t) * (prev_m - target) / (prev_m - m)
         prev_t, prev_m = t, m
     return 1.0
+
+
+def startup_model(ws, data, psd, det, metric, centre, mismatch, N, rank, M, eps, tail_degree=1, d_ref=100.0,
+                  squeeze=None, n_t=64, skip=0):
+    """The whole start-up in FP64 on the CPU: squeeze factor, Halton nodes,
+    overlaps, then the oracle Model (SVD per detector and mode, RBF fit of
+    the whitened node coordinates, frame x = A (theta - c))."""
+    from . import Model
+    kappa = squeeze if squeeze is not None else squeeze_factor(ws, psd[0], metric, centre, mismatch, n_t)
+    theta, y, A = place_nodes(metric, centre, mismatch, kappa, N, skip)
+    Z, S = node_overlaps(ws, theta, data, psd, M)
+    model = Model(y, Z, S, rank, eps, tail_degree, ws.modes, det, -(M // 2) * ws.dt, ws.dt, d_ref,
+                  centre=centre, frame=A)
+    return model, {"kappa": kappa, "theta": theta, "y": y, "frame": A}

@@ -15,7 +15,8 @@ import numpy as np
 from .build import SO as _SO_PATH, build
 
 __all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch", "Mlp",
-           "svd_compress", "FORMS", "pack_node_values", "nested_sample", "reweight"]
+           "svd_compress", "FORMS", "pack_node_values", "nested_sample", "reweight", "Wave", "place_nodes",
+           "squeeze_factor", "standin_overlaps"]
 
 MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
 MF_E_ILLCOND, MF_E_RANGE, MF_E_TIMEOUT, MF_E_NOTIMPL, MF_E_STATE = -4, -5, -6, -7, -8
@@ -48,6 +49,27 @@ class NsResult(ctypes.Structure):
                 ("accept", ctypes.c_double), ("scale", ctypes.c_double), ("wall_ms", ctypes.c_double),
                 ("n_samples", ctypes.c_longlong), ("n_like", ctypes.c_longlong), ("iterations", ctypes.c_int),
                 ("converged", ctypes.c_int), ("dim", ctypes.c_int)]
+
+
+class Wave(ctypes.Structure):
+    """mf_wave: the frequency-domain stand-in templates of the start-up."""
+    _fields_ = [("n_modes", ctypes.c_int), ("ell_m", (ctypes.c_int * 2) * 5), ("amp", ctypes.c_double * 5),
+                ("f_lo", ctypes.c_double), ("f_hi", ctypes.c_double), ("f_ref", ctypes.c_double),
+                ("powers", ctypes.c_double * 4), ("scales", ctypes.c_double * 4), ("cut_dir", ctypes.c_double * 4),
+                ("cut_rate", ctypes.c_double), ("L", ctypes.c_int), ("dt", ctypes.c_double)]
+
+    @classmethod
+    def make(cls, modes, amps, f_lo, f_hi, f_ref, powers, scales, cut_dir, cut_rate, L, dt):
+        w = cls()
+        w.n_modes = len(modes)
+        for i, (l, m) in enumerate(modes):
+            w.ell_m[i][0], w.ell_m[i][1] = int(l), int(m)
+            w.amp[i] = float(amps[i])
+        w.f_lo, w.f_hi, w.f_ref = float(f_lo), float(f_hi), float(f_ref)
+        for a in range(4):
+            w.powers[a], w.scales[a], w.cut_dir[a] = float(powers[a]), float(scales[a]), float(cut_dir[a])
+        w.cut_rate, w.L, w.dt = float(cut_rate), int(L), float(dt)
+        return w
 
 
 class MlpTrainParams(ctypes.Structure):
@@ -115,6 +137,10 @@ def lib():
         L.mf_mlp_query.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(dp)]
         L.mf_train_surrogate.argtypes = [vp, vp, ip, vp, vp, ip, ip, ctypes.POINTER(SurrogateParams),
                                          vp]
+        L.mf_set_frame.argtypes = [vp, vp, vp]
+        L.mf_place_nodes.argtypes = [vp, vp, dp, dp, ip, ctypes.c_longlong, vp, vp, vp]
+        L.mf_squeeze_factor.argtypes = [ctypes.POINTER(Wave), vp, vp, vp, dp, ip, ctypes.POINTER(dp), vp]
+        L.mf_standin_overlaps.argtypes = [ctypes.POINTER(Wave), vp, ip, vp, vp, ip, ip, vp, vp, vp]
         L.mf_nested_sample.argtypes = [vp, ctypes.POINTER(NsParams), ctypes.POINTER(NsResult), vp, vp, vp,
                                        ip, vp]
         L.mf_reweight.argtypes = [vp, vp, ip, vp, ctypes.POINTER(dp)]
@@ -151,6 +177,44 @@ def svd_compress(Z: np.ndarray, rank: int, stream=None):
                                  _stream_ptr(stream) if stream is not None else None),
            "mf_svd_compress")
     return coef, basis, sv
+
+
+def place_nodes(metric, centre, mismatch, squeeze, N, skip=0):
+    """mf_place_nodes: (theta [N,4], y [N,4] whitened, frame A [4,4])."""
+    g = np.ascontiguousarray(metric, dtype=np.float64)
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    th = np.empty((N, 4))
+    y = np.empty((N, 4))
+    A = np.empty((4, 4))
+    _check(lib().mf_place_nodes(_ptr(g), _ptr(c), float(mismatch), float(squeeze), int(N), int(skip), _ptr(th),
+                                _ptr(y), _ptr(A)), "mf_place_nodes")
+    return th, y, A
+
+
+def squeeze_factor(wave, psd, metric, centre, mismatch, n_t=64):
+    """mf_squeeze_factor: (kappa, match along the longest axis [n_t])."""
+    p = np.ascontiguousarray(psd, dtype=np.float64)
+    g = np.ascontiguousarray(metric, dtype=np.float64)
+    c = np.ascontiguousarray(centre, dtype=np.float64)
+    k = ctypes.c_double()
+    m = np.empty(n_t)
+    _check(lib().mf_squeeze_factor(ctypes.byref(wave), _ptr(p), _ptr(g), _ptr(c), float(mismatch), int(n_t),
+                                   ctypes.byref(k), _ptr(m)), "mf_squeeze_factor")
+    return k.value, m
+
+
+def standin_overlaps(wave, theta, data, psd, M, stream=None):
+    """mf_standin_overlaps: Z [n_det, n_modes, N, M] and sigma [n_det, N, nm, nm] (complex)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    d = np.ascontiguousarray(np.stack([np.real(data), np.imag(data)], -1), dtype=np.float64)
+    p = np.ascontiguousarray(psd, dtype=np.float64)
+    nd, N, nm = d.shape[0], th.shape[0], wave.n_modes
+    z = np.empty((nd, nm, N, M, 2))
+    sg = np.empty((nd, N, nm, nm, 2))
+    _check(lib().mf_standin_overlaps(ctypes.byref(wave), _ptr(th), N, _ptr(d), _ptr(p), nd, int(M), _ptr(z),
+                                     _ptr(sg), _stream_ptr(stream) if stream is not None else None),
+           "mf_standin_overlaps")
+    return z[..., 0] + 1j * z[..., 1], sg[..., 0] + 1j * sg[..., 1]
 
 
 def nested_sample(model, n_live=1000, batch=100, walks=150, dlogz=0.1, max_iter=100000, r_ball=0.9,
@@ -277,6 +341,47 @@ class Interpolant:
         _check(lib().mf_set_sky(self._h, _ptr(T), _ptr(P), None if t is None else _ptr(t), float(gmst0),
                                 float(omega), float(d_ref)), "mf_set_sky")
         self.sky = True
+
+    def set_frame(self, A, centre=None):
+        """mf_set_frame: x = A (theta - centre) with a general 4x4 map A."""
+        a = np.ascontiguousarray(A, dtype=np.float64)
+        c = None if centre is None else np.ascontiguousarray(centre, dtype=np.float64)
+        _check(lib().mf_set_frame(self._h, _ptr(a), None if c is None else _ptr(c)), "mf_set_frame")
+
+    @classmethod
+    def from_startup(cls, wave, data, psd, det, metric, centre, mismatch, N, rank, M, eps, modes, d_ref=100.0,
+                     tail_degree=1, form="fp32", squeeze=None, n_t=64, skip=0):
+        """The whole start-up on the GPU (Sec. II C): squeeze factor from the
+        match along the longest axis (unless given), Halton nodes in the
+        squeezed ellipsoid, node overlaps and cross terms by FFT, SVD per
+        (detector, mode), RBF fit in the whitened node coordinates.  Returns
+        (Interpolant, info) with info = dict(kappa, theta, y, frame, seconds)."""
+        import time
+        t0 = time.perf_counter()
+        kappa = squeeze if squeeze is not None else squeeze_factor(wave, psd[0], metric, centre, mismatch, n_t)[0]
+        t1 = time.perf_counter()
+        theta, y, A = place_nodes(metric, centre, mismatch, kappa, N, skip)
+        t2 = time.perf_counter()
+        Z, sigma = standin_overlaps(wave, theta, data, psd, M)
+        t3 = time.perf_counter()
+        nd, nm = Z.shape[:2]
+        coef = np.empty((nd, nm, N, rank), np.complex128)
+        basis = np.empty((nd, nm, rank, M), np.complex128)
+        for k in range(nd):
+            for j in range(nm):
+                coef[k, j], basis[k, j], _ = svd_compress(Z[k, j], rank)
+        t4 = time.perf_counter()
+        self = cls(y, pack_node_values(coef, sigma), eps, tail_degree)
+        self.set_layout(nd, nm, modes, rank)
+        self.set_basis(basis, -(M // 2) * wave.dt, wave.dt)
+        self.set_detectors(det, d_ref)
+        self.set_frame(A, centre)
+        self.set_form(form)
+        t5 = time.perf_counter()
+        info = {"kappa": kappa, "theta": theta, "y": y, "frame": A,
+                "seconds": {"squeeze": t1 - t0, "nodes": t2 - t1, "overlaps": t3 - t2, "svd": t4 - t3,
+                            "fit": t5 - t4}}
+        return self, info
 
     def set_rotation(self, metric=None, centre=None):
         m = None if metric is None else np.ascontiguousarray(metric, dtype=np.float64)

@@ -450,3 +450,19 @@ def make_startup_event(n_det: int = 3, seed: int = 7000, snr: float = 20.0, mism
         data[k, 0] = 0.0
     metric = model_metric(ws, psd[0])
     return StartupEvent(ws, psd, data, theta_inj, theta_inj.copy(), metric, det, mismatch)
+
+
+def queries_in_frame(frame, centre, Q: int, seed: int, radius: float = 0.9, tc_range: float = 5e-3):
+    """Q queries uniform in the ball of `radius` of the whitened coordinates
+    y = frame (theta - centre) (i.e. in the squeezed ellipsoid), mapped to
+    the sampler frame; extrinsics as make_queries.  FP32 [Q,4], [Q,5]."""
+    rng = np.random.default_rng(seed)
+    y = ball(rng, Q, r=radius)
+    theta = np.asarray(centre)[None, :] + y @ np.linalg.inv(np.asarray(frame)).T
+    ext = np.empty((Q, 5))
+    ext[:, 0] = rng.uniform(100.0, 400.0, Q)
+    ext[:, 1] = rng.uniform(-1.0, 1.0, Q)
+    ext[:, 2] = rng.uniform(0.0, np.pi, Q)
+    ext[:, 3] = rng.uniform(0.0, 2 * np.pi, Q)
+    ext[:, 4] = rng.uniform(-tc_range, tc_range, Q)
+    return theta.astype(np.float32), ext.astype(np.float32)
