@@ -592,6 +592,11 @@ int mf_set_option(mf_handle *h, const char *key, double value) {
         if (h->have_layout && mf::is_tc_form(h->form)) return mf::prepare_form(h, h->form);
         return MF_OK;
     }
+    if (k == "tc_pair") {
+        if (value != 0 && value != 1) return MF_E_INVAL;
+        h->tc_pair = (int)value;
+        return MF_OK;
+    }
     if (k == "tc_nbs") {
         int v = (int)value;
         if (v != 0 && (v < 2 || v > 6)) return MF_E_INVAL;

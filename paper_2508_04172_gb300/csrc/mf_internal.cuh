@@ -80,6 +80,7 @@ struct RotParams {
 // array (batched launch).
 struct TcEvent {
     CUtensorMap tm_hi, tm_lo;   // W_hi / W_lo [Kdev][Nk] K-major, box kKB x nbox
+    CUtensorMap tm_hi2, tm_lo2; // the same with half-height boxes (nbox / 2 rows): paired launch
     EpiParams epi;
     RotParams rot;
     const float4 *nodes_s;      // [Nk] nodes * (-pre), padding zero
@@ -87,6 +88,7 @@ struct TcEvent {
     int N, P;                   // nodes, tail monomials
     int nkb;                    // node blocks of 32 (Nk / 32)
     int nbox;                   // rows of one W tile = widest pass of this event
+    int pair_ok;                // half-height maps exist (nbox / 2 a multiple of 8 rows)
 };
 
 // Per-call arguments of a batched launch (kernel parameter; < 32 KB).
@@ -168,6 +170,10 @@ struct mf_handle {
     // tcgen05 forms: tensor maps (opaque 128-byte CUtensorMap) of W_hi / W_lo
     alignas(64) unsigned char tmap_hi[128];
     alignas(64) unsigned char tmap_lo[128];
+    alignas(64) unsigned char tmap_hi2[128];   // half-height boxes (paired launch)
+    alignas(64) unsigned char tmap_lo2[128];
+    bool pair_ok = false;           // the half-height maps exist
+    int tc_pair = 1;                // 1: pair two query tiles per cluster when possible, 0: never
     int nbox = 0;                   // rows (device columns) per W tile = widest pass
     // scratch
     unsigned long long *d_bad = nullptr;

@@ -66,6 +66,17 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, 
         "l"((uint64_t)tmap), "r"(x), "r"(y), "r"(su32(bar))
         : "memory");
 }
+// The same tile load delivered to the same shared-memory offset, completing
+// as transaction bytes on the same mbarrier offset, in every CTA of `mask`
+// (this GPU's own memory; all CTAs of one cluster).
+__device__ __forceinline__ void tma_load_2d_mc(void *dst, const void *tmap, int x, int y, uint64_t *bar,
+                                               uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
+        "l"((uint64_t)tmap), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
+        : "memory");
+}
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }

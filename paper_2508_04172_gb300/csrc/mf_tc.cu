@@ -40,6 +40,7 @@ struct TcCall {
     float *out, *partial;
     int Q, E;
     int n_tiles;            // query tiles of 128
+    int n_items;            // work items: tiles, or pairs of tiles (paired launch)
     int n_clusters;         // clusters launched (each loops over work items)
     int sb;                 // W ring depth
     int nbox_max;           // W ring slot rows
@@ -49,11 +50,12 @@ struct TcCall {
     int K;                  // columns-only launch: row stride of cols
 };
 
-// Work source of the single-event kernel: work item = query tile.
+// Work source of the single-event kernel: work item = query tile (or pair
+// of tiles, `tile` then being the pair index).
 struct SingleSrc {
     const TcEvent *ev;
     const TcCall *c;
-    __device__ __forceinline__ int n_items() const { return c->n_tiles; }
+    __device__ __forceinline__ int n_items() const { return c->n_items; }
     __device__ __forceinline__ void item(int it, int &e, int &tile) const {
         e = 0;
         tile = it;
@@ -128,7 +130,8 @@ struct NodeCursor {
 };
 
 template <class Src>
-__device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, int cid, int nc, int rank) {
+__device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, int cid, int nc, int rank, int pair,
+                                              int half) {
     while (cu.valid && cu.kb >= cu.nkb) {
         ++cu.r;
         const int it = item_of(cu.r, cid, nc);
@@ -140,7 +143,7 @@ __device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, in
         src.item(it, e, tile);
         const TcEvent &ev = src.event(e);
         cu.nkb = ev.nkb;
-        cu.rot = tile_rot(tile, ev.nkb);
+        cu.rot = tile_rot(tile * pair + half, ev.nkb);
         cu.nodes = ev.nodes_s;
         cu.kb = rank;
     }
@@ -174,7 +177,15 @@ __device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, in
 // COLS = true is the columns-only variant (mf_eval_columns): the epilogue
 // writes the pass's interpolated columns of each query to cols [Q][K] (user
 // column order via umap) instead of combining them into lnL.
-template <int NM, int AT, int TERMS, class Src, bool COLS = false>
+//
+// PAIR = 2 is the paired launch: a cluster of 2 np CTAs works on two query
+// tiles at once (cluster rank = half * np + pass).  The two CTAs of a pass
+// read the same weight tiles: each loads half of the tile's rows with a
+// multicast TMA into both CTAs' rings, and a ring slot is released when both
+// CTAs' MMAs have read it (the emptyB barriers count two commits).  The RBF
+// tiles are shared within each half as in the single launch.  Per query the
+// arithmetic, and its order, is that of the single launch.
+template <int NM, int AT, int TERMS, class Src, bool COLS = false, int PAIR = 1>
 __device__ __forceinline__ void tc_body(const Src &src, const int np, const int nbox_max, const int SB,
                                         const int nc, const int E, unsigned *err, float *cols = nullptr,
                                         const int *umap = nullptr, int K = 0) {
@@ -185,8 +196,12 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
     constexpr float kPhiLog2 = (AT == 0) ? 14.f : 0.f;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int rank = (int)(blockIdx.x % (unsigned)np);   // == %cluster_ctarank
-    const int cid = (int)(blockIdx.x / (unsigned)np);
+    const int crank = (int)(blockIdx.x % (unsigned)(PAIR * np));   // == %cluster_ctarank
+    const int rank = crank % np;          // column pass of this CTA
+    const int half = crank / np;          // tile of the pair
+    const int hbase = half * np;          // cluster rank of this half's pass 0
+    const uint16_t pairmask = (uint16_t)(PAIR == 2 ? ((1u << rank) | (1u << (np + rank))) : (1u << crank));
+    const int cid = (int)(blockIdx.x / (unsigned)(PAIR * np));
     const int btile = nbox_max * kRowBytes;
     const int nslot = np * SP;
     const int n_items = src.n_items();
@@ -211,7 +226,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
         }
         for (int i = 0; i < SB; ++i) {
             mbar_init(fullB + i, 1);
-            mbar_init(emptyB + i, 1);
+            mbar_init(emptyB + i, PAIR);   // released by the MMAs of both CTAs of the pass
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(tfull + i, 1);
@@ -251,15 +266,23 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                 src.item(it, e, tile);
                 const TcEvent &ev = src.event(e);
                 const int col0 = ev.epi.passes[rank].col0;
-                const uint32_t bytes = (uint32_t)(NB * ev.nbox * kRowBytes);
+                const uint32_t bytes = (uint32_t)(NB * ev.nbox * kRowBytes);   // the whole tile lands here
                 const int nkb = ev.nkb;
-                const int rot = tile_rot(tile, nkb);
+                const int rot = tile_rot(tile * PAIR + half, nkb);
+                const int hrows = ev.nbox / 2;                                  // paired: rows this CTA loads
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(emptyB + s, ph ^ 1, err, 1, kb)) { ok = false; break; }
                     mbar_expect_tx(fullB + s, bytes);
                     const int kx = rot_kb(kb, rot, nkb) * kKB;
-                    tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kx, col0, fullB + s);
-                    if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kx, col0, fullB + s);
+                    if (PAIR == 2) {
+                        uint8_t *d0 = sB + (s * NB + 0) * btile + half * hrows * kRowBytes;
+                        tma_load_2d_mc(d0, &ev.tm_hi2, kx, col0 + half * hrows, fullB + s, pairmask);
+                        if (NB == 2)
+                            tma_load_2d_mc(d0 + btile, &ev.tm_lo2, kx, col0 + half * hrows, fullB + s, pairmask);
+                    } else {
+                        tma_load_2d(sB + (s * NB + 0) * btile, &ev.tm_hi, kx, col0, fullB + s);
+                        if (NB == 2) tma_load_2d(sB + (s * NB + 1) * btile, &ev.tm_lo, kx, col0, fullB + s);
+                    }
                     ++issued;
                     if (++s == SB) { s = 0; ph ^= 1; }
                 }
@@ -310,8 +333,9 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                         if (TERMS >= 2) mma_f16(d, a + ko, b + dBlo + ko, id, 1u);
                         if (TERMS == 3) mma_f16(d, a + dAlo + ko, b + ko, id, 1u);
                     }
-                    mma_commit(emptyB + sb);
-                    mma_commit_mc(emptyA + sa, (uint16_t)(1u << p));   // slot read: tell its producer
+                    if (PAIR == 2) mma_commit_mc(emptyB + sb, pairmask);   // both CTAs' rings
+                    else mma_commit(emptyB + sb);
+                    mma_commit_mc(emptyA + sa, (uint16_t)(1u << (hbase + p)));   // slot read: tell its producer
                     if (p != rank) mbar_expect_tx(fullA + sa, abytes);   // arm the slot's next fill
                     use = (use & ~(3u << (2 * p))) | (((v + 1u) & 3u) << (2 * p));
                     if (++sb == SB) { sb = 0; pb ^= 1; }
@@ -343,19 +367,20 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
         // this lane's node of the next kNodeAhead node blocks of this CTA (FIFO)
         float4 yq[kNodeAhead];
         NodeCursor cu{-1, 0, 0, 0, nullptr, true};
-        cursor_settle(cu, src, cid, nc, rank);
+        cursor_settle(cu, src, cid, nc, rank, PAIR, half);
 #pragma unroll
         for (int dd = 0; dd < kNodeAhead; ++dd) {
             yq[dd] = cu.valid ? ldg_keep(cu.nodes + rot_kb(cu.kb, cu.rot, cu.nkb) * kKB + nperm)
                               : make_float4(0.f, 0.f, 0.f, 0.f);
             cu.kb += np;
-            cursor_settle(cu, src, cid, nc, rank);
+            cursor_settle(cu, src, cid, nc, rank, PAIR, half);
         }
         for (int r = 0; ok; ++r) {
             const int it = item_of(r, cid, nc);
             if (it >= n_items) break;
             int e, tile;
             src.item(it, e, tile);
+            tile = tile * PAIR + half;
             const TcEvent &ev = src.event(e);
             const EvIO io = src.io(e);
             const int N = ev.N, P = ev.P, nkb = ev.nkb;
@@ -387,7 +412,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                 yq[kNodeAhead - 1] = cu.valid ? ldg_keep(cu.nodes + rot_kb(cu.kb, cu.rot, cu.nkb) * kKB + nperm)
                                               : make_float4(0.f, 0.f, 0.f, 0.f);
                 cu.kb += np;
-                cursor_settle(cu, src, cid, nc, rank);
+                cursor_settle(cu, src, cid, nc, rank, PAIR, half);
                 float4 *scr = sN + ((warp - 2) * 2 + sbuf) * kKB;
                 sbuf ^= 1;
                 scr[lane] = ycur;
@@ -465,7 +490,8 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                     // as transaction bytes on their (pre-armed) fullA barrier
                     const uint32_t src_a = su32(base), fa = su32(fullA + sa);
                     for (int dst = 0; dst < np; ++dst)
-                        if (dst != rank) bulk_copy_to_cta(map_cta(src_a, dst), src_a, abytes, map_cta(fa, dst));
+                        if (dst != rank)
+                            bulk_copy_to_cta(map_cta(src_a, hbase + dst), src_a, abytes, map_cta(fa, hbase + dst));
                     mbar_arrive(fullA + sa);
                 }
                 ++u;
@@ -480,6 +506,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
             if (it >= n_items) break;
             int e, tile;
             src.item(it, e, tile);
+            tile = tile * PAIR + half;
             const TcEvent &ev = src.event(e);
             const EvIO io = src.io(e);
             const Pass ps = ev.epi.passes[rank];
@@ -526,12 +553,12 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
     }
 }
 
-template <int NM, int AT, int TERMS, bool COLS = false>
+template <int NM, int AT, int TERMS, bool COLS = false, int PAIR = 1>
 __global__ void __launch_bounds__(kThreads, 1)
 tc_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ TcCall call) {
     SingleSrc src{&ev, &call};
-    tc_body<NM, AT, TERMS, SingleSrc, COLS>(src, ev.epi.n_pass, call.nbox_max, call.sb, call.n_clusters, call.E,
-                                           call.err, call.cols, call.umap, call.K);
+    tc_body<NM, AT, TERMS, SingleSrc, COLS, PAIR>(src, ev.epi.n_pass, call.nbox_max, call.sb, call.n_clusters,
+                                                 call.E, call.err, call.cols, call.umap, call.K);
 }
 
 template <int NM, int AT, int TERMS>
@@ -630,6 +657,21 @@ void *pick_cols_kernel(mf_form f) {
                                                                           : (void *)tc_kernel<1, 0, 3, true>;
     return terms == 1 ? (void *)tc_kernel<1, 1, 1, true> : terms == 2 ? (void *)tc_kernel<1, 1, 2, true>
                                                                       : (void *)tc_kernel<1, 1, 3, true>;
+}
+// Paired launch (3-term forms, lnL kernels only).
+template <int NM>
+void *pick_pair1(int at) { return at == 0 ? (void *)tc_kernel<NM, 0, 3, false, 2> : (void *)tc_kernel<NM, 1, 3, false, 2>; }
+void *pick_pair_kernel(mf_form f, int n_modes) {
+    if (form_terms(f) != 3) return nullptr;
+    const int at = form_type(f);
+    switch (n_modes) {
+        case 1: return pick_pair1<1>(at);
+        case 2: return pick_pair1<2>(at);
+        case 3: return pick_pair1<3>(at);
+        case 4: return pick_pair1<4>(at);
+        case 5: return pick_pair1<5>(at);
+        default: return nullptr;
+    }
 }
 void *pick_kernel(mf_form f, int n_modes, bool batch) {
     const int at = form_type(f), terms = form_terms(f);
@@ -735,7 +777,19 @@ int convert_tc_weights(mf_handle *h, mf_form f) {
     MF_CUDA(e);
     int rc = make_tmap(h->tmap_hi, h->d_Whi, at, h->Nk, h->Kdev, nbox);
     if (rc) return rc;
-    return make_tmap(h->tmap_lo, h->d_Wlo, at, h->Nk, h->Kdev, nbox);
+    rc = make_tmap(h->tmap_lo, h->d_Wlo, at, h->Nk, h->Kdev, nbox);
+    if (rc) return rc;
+    // half-height boxes for the paired launch: each half a whole number of
+    // 8-row swizzle atoms, so the two halves tile the ring slot exactly
+    h->pair_ok = false;
+    if (nbox % 16 == 0) {
+        rc = make_tmap(h->tmap_hi2, h->d_Whi, at, h->Nk, h->Kdev, nbox / 2);
+        if (rc) return rc;
+        rc = make_tmap(h->tmap_lo2, h->d_Wlo, at, h->Nk, h->Kdev, nbox / 2);
+        if (rc) return rc;
+        h->pair_ok = true;
+    }
+    return MF_OK;
 }
 
 int fill_tc_event(const mf_handle *h, TcEvent *ev) {
@@ -743,6 +797,11 @@ int fill_tc_event(const mf_handle *h, TcEvent *ev) {
     memset(ev, 0, sizeof(*ev));
     memcpy(&ev->tm_hi, h->tmap_hi, sizeof(CUtensorMap));
     memcpy(&ev->tm_lo, h->tmap_lo, sizeof(CUtensorMap));
+    if (h->pair_ok) {
+        memcpy(&ev->tm_hi2, h->tmap_hi2, sizeof(CUtensorMap));
+        memcpy(&ev->tm_lo2, h->tmap_lo2, sizeof(CUtensorMap));
+    }
+    ev->pair_ok = h->pair_ok ? 1 : 0;
     ev->epi = make_epi(h);
     ev->rot = make_rot(h);
     ev->nodes_s = h->d_nodes_s;
@@ -792,7 +851,12 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
     if (!h->d_Whi) return MF_E_STATE;
     const int np = (int)h->passes.size();
     if (np > kMaxCluster) return MF_E_NOTIMPL;
-    void *kern = cols ? pick_cols_kernel(h->form) : pick_kernel(h->form, h->n_modes, false);
+    // paired launch: two query tiles per cluster sharing the weight tiles
+    // (cluster of 2 np <= 8 CTAs), for the 3-term lnL kernels
+    const bool pair = !cols && h->tc_pair && h->pair_ok && 2 * np <= kMaxCluster && form_terms(h->form) == 3 &&
+                      Q > kTile;
+    void *kern = cols ? pick_cols_kernel(h->form)
+                      : pair ? pick_pair_kernel(h->form, h->n_modes) : pick_kernel(h->form, h->n_modes, false);
     if (!kern) return MF_E_NOTIMPL;
     TcEvent ev;
     int rc = fill_tc_event(h, &ev);
@@ -809,6 +873,7 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
     c.Q = Q;
     c.E = E;
     c.n_tiles = (Q + kTile - 1) / kTile;
+    c.n_items = pair ? (c.n_tiles + 1) / 2 : c.n_tiles;
     c.nbox_max = h->nbox;
     c.err = h->d_err;
     c.sb = h->tc_nbs ? h->tc_nbs : 4;
@@ -818,10 +883,11 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[1];
     int maxc = 0;
-    rc = tc_config(kern, np, smem, st, cfg, attr, &maxc);
+    const int cl = pair ? 2 * np : np;
+    rc = tc_config(kern, cl, smem, st, cfg, attr, &maxc);
     if (rc) return rc;
-    c.n_clusters = std::min(c.n_tiles, maxc);
-    cfg.gridDim = dim3((unsigned)(c.n_clusters * np), 1, 1);
+    c.n_clusters = std::min(c.n_items, maxc);
+    cfg.gridDim = dim3((unsigned)(c.n_clusters * cl), 1, 1);
     void *args[2] = {(void *)&ev, (void *)&c};
     MF_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
     return MF_OK;
