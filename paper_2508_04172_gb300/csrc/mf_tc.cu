@@ -92,11 +92,12 @@ struct BatchSrc {
 // decreasing cost the clusters' totals stay close.
 //
 // Node-block order of a tile: the k-loop of tile t starts at block
-// rot = 11 t mod nkb and wraps around, so that the clusters (which start
-// together) do not all fetch the same weight tile at the same time.  The
-// order depends only on the tile, so a query's sum is formed in the same
-// order whatever the launch shape.
-__device__ __forceinline__ int tile_rot(int tile, int nkb) { return (int)(((long long)tile * 11) % nkb); }
+// rot = 11 floor(t / 2) mod nkb and wraps around, so that the clusters
+// (which start together) do not all fetch the same weight tile at the same
+// time.  Tiles 2i and 2i+1 share the order (the paired launch gives both the
+// same weight tiles); the order depends only on the tile, so a query's sum
+// is formed in the same order whatever the launch shape.
+__device__ __forceinline__ int tile_rot(int tile, int nkb) { return (int)(((long long)(tile >> 1) * 11) % nkb); }
 __device__ __forceinline__ int rot_kb(int kb, int rot, int nkb) {
     const int k = kb + rot;
     return k >= nkb ? k - nkb : k;

@@ -77,9 +77,9 @@ struct Tc2Call {
 
 // COLS = true: columns-only variant (mf_eval_columns), the epilogue writes
 // each pass's interpolated columns instead of combining them into lnL.
-// Node-block order of tile t: starts at 11 t mod nkb and wraps (the same
-// order as the cluster design, so the two give bitwise equal sums).
-__device__ __forceinline__ int tile_rot2(int tile, int nkb) { return (int)(((long long)tile * 11) % nkb); }
+// Node-block order of tile t: starts at 11 floor(t / 2) mod nkb and wraps
+// (the same order as the cluster design, so the two give bitwise equal sums).
+__device__ __forceinline__ int tile_rot2(int tile, int nkb) { return (int)(((long long)(tile >> 1) * 11) % nkb); }
 
 template <int NM, int AT, int TERMS, bool COLS = false>
 __global__ void __launch_bounds__(kThreads2, 1)
