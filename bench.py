@@ -447,11 +447,13 @@ def run_kernels_only(args):
             m.loglike(d_th, d_ex, out=d_out)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push(f"timed_{f}")
         e0.record()
         for _ in range(args.steps):
             m.loglike(d_th, d_ex, out=d_out)
         e1.record()
         e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         rc, n_bad = m.sync_status()
         print(json.dumps({"kernels_only": spec.name, "form": f, "ms_per_launch":
                           round(e0.elapsed_time(e1) / args.steps, 4), "status": rc, "n_bad": n_bad}),
