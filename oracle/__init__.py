@@ -9,7 +9,10 @@ online stage is written out as loops in ``mforacle.c``.
 
 Paper map:
   * ``svd_compress``      -- Eq. (SVD): SVD of the node-by-time overlap matrix.
-  * ``rbf_fit``           -- Eq. (rbfcoeff) with the side condition P^T a = 0.
+  * ``rbf_fit``           -- Eq. (rbfcoeff) with the side condition P^T a = 0,
+                             for the Gaussian, cubic polyharmonic (PHS3),
+                             multiquadric (MQ) and inverse multiquadric (IMQ)
+                             radial kernels.
   * ``metric_rotation``   -- Sec. II D: Delta-e = displacement along the metric
                              eigenvectors, smallest eigenvalue first.
   * ``Model.loglike``     -- Sec. II D online stage + Eq. (logl_complete).
@@ -54,7 +57,7 @@ class _Model(ctypes.Structure):
                 ("d_ref", ctypes.c_double), ("R", ctypes.c_void_p), ("centre", ctypes.c_void_p),
                 ("stencil", ctypes.c_int), ("sky", ctypes.c_int), ("dtensor", ctypes.c_void_p),
                 ("dpos", ctypes.c_void_p), ("tau", ctypes.c_void_p), ("gmst0", ctypes.c_double),
-                ("omega_e", ctypes.c_double)]
+                ("omega_e", ctypes.c_double), ("rbf", ctypes.c_int)]
 
 
 def lib():
@@ -115,23 +118,61 @@ def svd_compress(Z: np.ndarray, rank: int):
     return C, B, s
 
 
-def tail_size(tail_degree: int) -> int:
-    """M = C(r + d, r) monomials for degree r in d = 4 (Eq. rbfcoeff)."""
-    return {-1: 0, 0: 1, 1: 5}[tail_degree]
+def tail_size(tail_degree: int, d: int = 4) -> int:
+    """M = C(r + d, r) monomials for degree r in dimension d (Eq. rbfcoeff;
+    d = 4 here, other d only for the pins)."""
+    return {-1: 0, 0: 1, 1: 1 + d}[tail_degree]
 
 
-def rbf_matrix(X: np.ndarray, Y: np.ndarray, eps: float) -> np.ndarray:
+# Radial kernels, in the order of the C ABI's enum (mf_rbf).  With s = eps r:
+#   gaussian  exp(-s^2)           positive definite
+#   phs3      s^3                 conditionally positive definite of order 2
+#   mq        sqrt(1 + s^2)       conditionally (negative) definite of order 1
+#   imq       1 / sqrt(1 + s^2)   positive definite
+# (for PHS3, eps only scales the kernel: the interpolant does not depend on it).
+RBF_KERNELS = ("gaussian", "phs3", "mq", "imq")
+_CPD_ORDER = {"gaussian": 0, "phs3": 2, "mq": 1, "imq": 0}
+
+
+def rbf_kernel_id(kernel) -> int:
+    return kernel if isinstance(kernel, int) else RBF_KERNELS.index(kernel)
+
+
+def min_tail_degree(kernel) -> int:
+    """Eq. (rbfcoeff) and the sentence after it: a kernel conditionally
+    positive definite of order r needs the monomials of degree r - 1 or more
+    for a unique interpolant (-1: no tail needed)."""
+    return _CPD_ORDER[RBF_KERNELS[rbf_kernel_id(kernel)]] - 1
+
+
+def rbf_phi(r2: np.ndarray, eps: float, kernel="gaussian") -> np.ndarray:
+    """phi(r) at squared distances r2 for the kernel (table above)."""
+    s2 = (eps * eps) * np.asarray(r2, dtype=np.float64)
+    k = RBF_KERNELS[rbf_kernel_id(kernel)]
+    if k == "gaussian":
+        return np.exp(-s2)
+    if k == "phs3":
+        return s2 * np.sqrt(s2)
+    if k == "mq":
+        return np.sqrt(1.0 + s2)
+    return 1.0 / np.sqrt(1.0 + s2)
+
+
+def rbf_matrix(X: np.ndarray, Y: np.ndarray, eps: float, kernel="gaussian") -> np.ndarray:
     d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
-    return np.exp(-(eps * eps) * d2)
+    return rbf_phi(d2, eps, kernel)
 
 
-def rbf_fit(nodes: np.ndarray, F: np.ndarray, eps: float, tail_degree: int = 1):
+def rbf_fit(nodes: np.ndarray, F: np.ndarray, eps: float, tail_degree: int = 1, kernel="gaussian"):
     """Eq. (rbfcoeff): solve [Phi P; P^T 0][a; b] = [F; 0] in FP64 (dense
-    LAPACK solve).  Returns W = [a; b] of shape [N+P, K]."""
-    N = nodes.shape[0]
-    P = tail_size(tail_degree)
+    LAPACK solve), tail monomials 1, x_1 .. x_d.  Returns W = [a; b] of shape
+    [N+P, K].  The tail degree must be at least min_tail_degree(kernel)."""
+    if tail_degree < min_tail_degree(kernel):
+        raise ValueError(f"kernel {kernel} needs a tail of degree >= {min_tail_degree(kernel)}")
+    N, d = nodes.shape
+    P = tail_size(tail_degree, d)
     A = np.zeros((N + P, N + P))
-    A[:N, :N] = rbf_matrix(nodes, nodes, eps)
+    A[:N, :N] = rbf_matrix(nodes, nodes, eps, kernel)
     if P:
         Pm = np.concatenate([np.ones((N, 1)), nodes], axis=1)[:, :P]
         A[:N, N:] = Pm
@@ -139,6 +180,23 @@ def rbf_fit(nodes: np.ndarray, F: np.ndarray, eps: float, tail_degree: int = 1):
     rhs = np.zeros((N + P, F.shape[1]))
     rhs[:N] = F
     return np.linalg.solve(A, rhs)
+
+
+def rbf_evaluate(nodes, W, eps, tail_degree, x, kernel="gaussian"):
+    """The interpolant [a; b] = W of rbf_fit at points x [Q, 4] -> [Q, K],
+    through the loops of mforacle.c (the evaluation the online stage uses)."""
+    nodes = np.ascontiguousarray(nodes, dtype=np.float64)
+    W = np.ascontiguousarray(W, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    N, K = nodes.shape[0], W.shape[1]
+    P = tail_size(tail_degree)
+    assert W.shape[0] == N + P
+    m = _Model()
+    m.N, m.K, m.P = N, K, P
+    m.nodes, m.W, m.eps, m.rbf = nodes.ctypes.data, W.ctypes.data, float(eps), rbf_kernel_id(kernel)
+    f = np.empty((x.shape[0], K))
+    lib().oracle_rbf_eval(ctypes.byref(m), x.shape[0], _dp(x), _dp(f))
+    return f
 
 
 def metric_rotation(metric) -> np.ndarray:
@@ -180,10 +238,11 @@ class Model:
     overlaps: per-(det, mode) SVD, one RBF fit for all columns, rotation."""
 
     def __init__(self, nodes, Z, sigma, rank, eps, tail_degree, modes, det, t0, dt,
-                 d_ref, metric=None, centre=None, stencil=10, sky=None, frame=None):
+                 d_ref, metric=None, centre=None, stencil=10, sky=None, frame=None, kernel="gaussian"):
         nd, nm, N, M = Z.shape
         self.nodes = np.ascontiguousarray(nodes, dtype=np.float64)
         self.rank, self.eps, self.tail_degree = rank, float(eps), tail_degree
+        self.kernel = RBF_KERNELS[rbf_kernel_id(kernel)]
         self.modes = tuple(tuple(m) for m in modes)
         self.n_det, self.n_modes, self.M = nd, nm, M
         C = np.empty((nd, nm, N, rank), complex)
@@ -194,7 +253,7 @@ class Model:
                 C[k, j], B[k, j], self.sv[k, j] = svd_compress(Z[k, j], rank)
         self.C, self.B = C, B
         self.F = pack_node_values(C, sigma)
-        self.W = np.ascontiguousarray(rbf_fit(self.nodes, self.F, eps, tail_degree))
+        self.W = np.ascontiguousarray(rbf_fit(self.nodes, self.F, eps, tail_degree, self.kernel))
         self.basis = np.ascontiguousarray(np.stack([B.real, B.imag], axis=-1))
         self.det = np.ascontiguousarray(det, dtype=np.float64)
         self.t0, self.dt, self.d_ref = float(t0), float(dt), float(d_ref)
@@ -235,7 +294,7 @@ class Model:
         s = ev.spec
         return cls(ev.nodes, node_overlaps(ev), standin_sigma(ev, ev.nodes), s.rank, s.eps,
                    s.tail_degree, s.modes, ev.det, s.t0, s.dt, s.d_ref, ev.metric, ev.centre,
-                   sky=getattr(ev, "sky", None))
+                   sky=getattr(ev, "sky", None), kernel=getattr(s, "kernel", "gaussian"))
 
     @property
     def K(self):
@@ -252,7 +311,7 @@ class Model:
                       self.basis.ctypes.data, self.t0, self.dt, self.det.ctypes.data,
                       self.d_ref, self.R.ctypes.data, self.centre.ctypes.data, self.stencil,
                       0 if self.sky is None else 1, self._dtensor.ctypes.data, self._dpos.ctypes.data,
-                      self._tau.ctypes.data, self._gmst0, self._omega)
+                      self._tau.ctypes.data, self._gmst0, self._omega, rbf_kernel_id(self.kernel))
 
     def rotate(self, theta):
         return (np.asarray(theta, np.float64) - self.centre) @ self.R.T

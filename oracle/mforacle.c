@@ -28,7 +28,7 @@ typedef struct {
     int N, K, P;            /* nodes, interpolated columns, tail terms (0,1,5) */
     const double *nodes;    /* [N][4] nodes in the metric eigenbasis            */
     const double *W;        /* [(N+P)][K] RBF weights a (N rows) then tail b    */
-    double eps;             /* Gaussian shape: phi(r) = exp(-(eps r)^2)         */
+    double eps;             /* shape parameter of the radial kernel (rbf below)  */
     int n_det, n_modes, rank, M;
     const int *ell_m;       /* [n_modes][2]                                     */
     const double *basis;    /* [n_det][n_modes][rank][M][2] (re, im)            */
@@ -47,6 +47,10 @@ typedef struct {
     const double *tau;      /* [n_det] epoch of channel k relative to t_c (s)    */
     double gmst0;           /* Greenwich sidereal angle at t_c = 0 (rad)         */
     double omega_e;         /* Earth's sidereal rotation rate (rad/s)            */
+    int rbf;                /* radial kernel, s = eps r: 0 Gaussian exp(-s^2),
+                             * 1 cubic polyharmonic s^3, 2 multiquadric
+                             * sqrt(1 + s^2), 3 inverse multiquadric
+                             * 1 / sqrt(1 + s^2)                                 */
 } oracle_model;
 
 /* ---------------------------------------------------------------- helpers */
@@ -141,13 +145,24 @@ static void rotate(const oracle_model *m, const double *theta, double *x) {
     }
 }
 
+/* The radial kernel phi(r) at squared distance r2 (Eq. rbfcoeff). */
+static double rbf_phi(const oracle_model *m, double r2) {
+    double s2 = m->eps * m->eps * r2;
+    switch (m->rbf) {
+        case 1: return s2 * sqrt(s2);
+        case 2: return sqrt(1.0 + s2);
+        case 3: return 1.0 / sqrt(1.0 + s2);
+        default: return exp(-s2);
+    }
+}
+
 /* Eq. (rbfcoeff): f_k(x) = sum_n a_nk phi(|x - y_n|) + sum_p b_pk p_p(x). */
 static void rbf_eval_point(const oracle_model *m, const double *x, double *f) {
     for (int k = 0; k < m->K; ++k) f[k] = 0.0;
     for (int n = 0; n < m->N; ++n) {
         double r2 = 0.0;
         for (int i = 0; i < 4; ++i) { double d = x[i] - m->nodes[n * 4 + i]; r2 += d * d; }
-        double phi = exp(-m->eps * m->eps * r2);
+        double phi = rbf_phi(m, r2);
         const double *w = m->W + (size_t)n * m->K;
         for (int k = 0; k < m->K; ++k) f[k] += phi * w[k];
     }

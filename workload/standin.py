@@ -70,6 +70,7 @@ class Spec:
     seed: int = 0
     sky: str = ""              # "": frozen patterns; "hlv" / "et": per-query (alpha, delta)
     epochs: tuple = ()         # per channel epoch offsets (s) of frequency bands, sky "et"
+    kernel: str = "gaussian"   # radial kernel: gaussian, phs3, mq, imq
 
     @property
     def n_modes(self) -> int:
