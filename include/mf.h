@@ -54,8 +54,19 @@ enum {
     MF_E_STATE = -8     /* handle not fully configured for this call           */
 };
 
-/* Radial kernel of Eq. (rbfcoeff).  Gaussian phi(r) = exp(-(eps r)^2). */
-typedef enum { MF_RBF_GAUSSIAN = 0 } mf_rbf;
+/* Radial kernel phi of Eq. (rbfcoeff), with s = eps r:
+ *   MF_RBF_GAUSSIAN  exp(-s^2)          positive definite (any tail)
+ *   MF_RBF_PHS3      s^3                cubic polyharmonic spline; conditionally
+ *                                       positive definite of order 2: needs the
+ *                                       affine tail (tail_degree 1); eps only
+ *                                       scales it
+ *   MF_RBF_MQ        sqrt(1 + s^2)      multiquadric; conditionally definite of
+ *                                       order 1: needs tail_degree >= 0
+ *   MF_RBF_IMQ       1 / sqrt(1 + s^2)  inverse multiquadric; positive definite
+ * (the paper's rule after Eq. rbfcoeff: order r needs monomials of degree
+ * r - 1 or more).  The FP16 forms take only the kernels bounded by 1
+ * (Gaussian, IMQ); BF16 and FP32 forms take all four. */
+typedef enum { MF_RBF_GAUSSIAN = 0, MF_RBF_PHS3 = 1, MF_RBF_MQ = 2, MF_RBF_IMQ = 3 } mf_rbf;
 
 /* Arithmetic of the Phi.W contraction (the interpolant evaluation).
  *   FP32        : FP32 SIMT FMAs (the plain form).
@@ -88,7 +99,17 @@ MF_API const char *mf_version(void);
  *   basis  : host out, [rank][M][2]  -- orthonormal u_i (rows of V^H),
  *            ordered by decreasing singular value.
  *   sv     : host out or NULL, [rank] singular values.
- * Runs on the GPU in FP64 (dense SVD, then projection C = Z V).  Synchronous.
+ * Runs on the GPU in FP64 with the library's own kernels: block subspace
+ * iteration on Z with rank + 10 columns (Gram-Schmidt applied twice, a
+ * one-sided Jacobi SVD of the small triangular factor), until the leading
+ * `rank` right singular vectors, weighted by their singular values, change
+ * by less than 1e-12 s_1 between iterations (at most 30 iterations); then
+ * C = Z V.  The singular values are accurate to rounding of s_1 (Z^H Z is
+ * never formed).  Deterministic: the start block is a fixed pseudo-random
+ * pattern and every reduction has a fixed order.  The basis is orthonormal
+ * even when Z has rank r < rank (for instance Z = 0): the rows beyond r then
+ * complete the set, with singular values and coefficients at rounding level
+ * (0 for Z = 0).  Synchronous.
  * Requires N >= M (at least as many nodes as time samples),
  * 1 <= rank <= M <= 8192.
  */
@@ -104,11 +125,17 @@ MF_API int mf_svd_compress(const double *z, int N, int M, int rank, double *coef
  *                 terms sigma: n_modes real diagonals, Re of the strict upper
  *                 triangle (row-major), Im of the strict upper triangle.
  *   rbf, eps    : radial kernel and shape parameter (eps > 0).
- *   tail_degree : -1 (none), 0 (constant) or 1 (affine: 1, x1..x4).
- * Solves [Phi P; P^T 0][a; b] = [F; 0] on the GPU in FP64 (Cholesky of Phi
- * plus the tail Schur complement) and estimates cond(Phi).  Returns
- * MF_E_ILLCOND if Phi is not numerically positive definite.  Synchronous on
- * `stream`.  Limits: 1 <= N <= 65536, 1 <= K <= 4096.
+ *   tail_degree : -1 (none), 0 (constant) or 1 (affine: 1, x1..x4); at
+ *                 least the kernel's minimum (mf_rbf), else MF_E_INVAL.
+ * Solves [Phi P; P^T 0][a; b] = [F; 0] on the GPU in FP64 with the
+ * library's own kernels.  Positive definite kernels (Gaussian, IMQ):
+ * Cholesky of Phi plus the tail Schur complement; cond = cond(Phi).
+ * Conditionally definite kernels (PHS3, MQ): the null-space method, Q R = P
+ * (Householder), Cholesky of the projected +/-(Q^T Phi Q) on the null space
+ * of P^T, then the tail coefficients from R; cond = that of the projected
+ * matrix.  Returns MF_E_ILLCOND if the (projected) matrix is not numerically
+ * positive definite, e.g. for duplicate nodes.  Synchronous on `stream`.
+ * Limits: 1 <= N <= 65536, 1 <= K <= 4096; N > number of tail terms.
  */
 MF_API int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rbf rbf,
              double eps, int tail_degree, void *stream, mf_handle **out);
@@ -534,13 +561,25 @@ MF_API int mf_reweight(const double *logwt, const double *log_ratio, int n, doub
  *   "pass_max" : widest column pass (16..512, multiple of 16) the tcgen05
  *                forms may use; re-lays out the weights.
  *   "tc_design": tcgen05 kernel design: 0 = thread-block clusters sharing
- *                the RBF tile in shared memory; 1 = the RBF tile in tensor
+ *                the RBF tile in shared memory (one launch per run of at
+ *                most "tc_chunk" passes); 1 = the RBF tile in tensor
  *                memory, one CTA per column pass (passes <= 192 columns);
  *                -1 (default) = 1 when the columns fit in one such pass,
  *                else 0.  Re-lays out the weights; mf_query "tc_design"
  *                reports the design in use.
  *   "tc_nbs"   : depth (2..4) of the weight-tile ring of the tcgen05 kernel;
  *                0 (default) = deepest that fits in shared memory.
+ *   "tc_pair"  : 1 (default) = the 3-term forms pair two query tiles per
+ *                cluster when 2 x passes <= 8 (weight tiles multicast to
+ *                both) and the larger clusters keep at least 93 % of the
+ *                resident CTAs of the single launch (mf_query "tc_paired"
+ *                tells the last launch's choice); 0 = never.  Results are
+ *                the same either way.
+ *   "tc_chunk" : passes per cluster launch at most (2..8); 0 (default) = as
+ *                many as one CTA's shared memory stages (4 for the 3-term
+ *                forms).  Columns needing more passes run as several
+ *                launches, each over a run of passes; results are the same
+ *                for every value.
  *   "pass_count": 0 (default) = as few column passes as "pass_max" allows;
  *                1..8 = exactly this many for the tcgen05 forms (contiguous
  *                groups, widest pass minimised; the FP32 form keeps its own

@@ -253,6 +253,14 @@ def reweight(logwt, log_ratio=None):
     return w, ne.value
 
 
+# mf_rbf: radial kernels in the order of the C enum
+RBF_KERNELS = ("gaussian", "phs3", "mq", "imq")
+
+
+def rbf_kernel_id(kernel) -> int:
+    return kernel if isinstance(kernel, int) else RBF_KERNELS.index(kernel)
+
+
 def pack_node_values(coef: np.ndarray, sigma: np.ndarray) -> np.ndarray:
     """Arrange SVD coefficients [n_det, n_modes, N, rank] (complex) and cross
     terms [n_det, N, n_modes, n_modes] (complex Hermitian) into the [N, K]
@@ -282,30 +290,32 @@ class Interpolant:
     """Owns an mf_handle: interpolants built on the GPU plus layout, basis,
     detectors, rotation and the selected arithmetic form."""
 
-    def __init__(self, nodes, node_values, eps, tail_degree=1, stream=None):
+    def __init__(self, nodes, node_values, eps, tail_degree=1, stream=None, kernel="gaussian"):
         nodes = np.ascontiguousarray(nodes, dtype=np.float64)
         F = np.ascontiguousarray(node_values, dtype=np.float64)
         self.N, self.K = F.shape
         self.tail_degree = int(tail_degree)
+        self.kernel = kernel
         h = ctypes.c_void_p()
-        _check(lib().mf_build(_ptr(nodes), _ptr(F), self.N, self.K, 0, float(eps),
+        _check(lib().mf_build(_ptr(nodes), _ptr(F), self.N, self.K, rbf_kernel_id(kernel), float(eps),
                               int(tail_degree), _stream_ptr(stream) if stream is not None else None,
                               ctypes.byref(h)), "mf_build")
         self._h = h
 
     @classmethod
     def from_overlaps(cls, nodes, Z, sigma, rank, eps, modes, det, t0, dt, d_ref,
-                      metric=None, centre=None, tail_degree=1, form="fp32", sky=None):
+                      metric=None, centre=None, tail_degree=1, form="fp32", sky=None, kernel="gaussian"):
         """Full start-up on the GPU from node overlaps Z [n_det, n_modes, N, M]
         (complex) and cross terms sigma [n_det, N, n_modes, n_modes]; sky: None
-        (frozen patterns det) or dict(tensor, pos, tau, gmst0, omega)."""
+        (frozen patterns det) or dict(tensor, pos, tau, gmst0, omega); kernel:
+        one of RBF_KERNELS (mf_rbf)."""
         nd, nm, N, M = Z.shape
         coef = np.empty((nd, nm, N, rank), np.complex128)
         basis = np.empty((nd, nm, rank, M), np.complex128)
         for k in range(nd):
             for j in range(nm):
                 coef[k, j], basis[k, j], _ = svd_compress(Z[k, j], rank)
-        self = cls(nodes, pack_node_values(coef, sigma), eps, tail_degree)
+        self = cls(nodes, pack_node_values(coef, sigma), eps, tail_degree, kernel=kernel)
         self.set_layout(nd, nm, modes, rank)
         self.set_basis(basis, t0, dt)
         if sky is None:

@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     if force or _stale(SO, objs):
         tmp = SO + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + [
-            "-lcusolver", "-lcublas", "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
+            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

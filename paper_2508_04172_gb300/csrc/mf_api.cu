@@ -249,7 +249,8 @@ RotParams make_rot(const mf_handle *h) {
     RotParams r;
     for (int i = 0; i < 16; ++i) r.R[i] = (float)h->R[i];
     for (int i = 0; i < 4; ++i) r.centre[i] = (float)h->centre[i];
-    r.pre = (float)(h->eps * std::sqrt(1.0 / std::log(2.0)));
+    r.pre = (float)rbf_prescale(h);
+    r.rbf = (int)h->rbf;
     return r;
 }
 
@@ -270,6 +271,10 @@ int prepare_form(mf_handle *h, mf_form f) {
         h->form = MF_FORM_MLP;
         return MF_OK;
     }
+    // FP16 forms scale Phi by 2^14: only kernels bounded by 1 fit their range
+    if ((f == MF_FORM_FP16 || f == MF_FORM_FP16_WSPLIT || f == MF_FORM_FP16_3TERM) &&
+        (h->rbf == MF_RBF_PHS3 || h->rbf == MF_RBF_MQ))
+        return MF_E_NOTIMPL;
     free_form(h);
     h->pass_count = is_tc_form(f) ? h->pass_count_user : 0;   // exact counts: tcgen05 forms only
     // tcgen05 design: the TMEM design when asked for, or (automatic) when the
@@ -304,8 +309,7 @@ int prepare_form(mf_handle *h, mf_form f) {
     if (h->d_nodes_s) cudaFree(h->d_nodes_s);
     h->d_nodes_s = nullptr;
     MF_CUDA(cudaMalloc((void **)&h->d_nodes_s, sizeof(float4) * (size_t)h->Nk));
-    prescale_nodes<<<(h->Nk + 255) / 256, 256>>>(h->d_nodes64, h->N, h->Nk,
-                                                 h->eps * std::sqrt(1.0 / std::log(2.0)),
+    prescale_nodes<<<(h->Nk + 255) / 256, 256>>>(h->d_nodes64, h->N, h->Nk, rbf_prescale(h),
                                                  h->d_nodes_s);
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaDeviceSynchronize());
@@ -350,7 +354,9 @@ int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rb
     if (!nodes || !node_values || N < 1 || N > 65536 || K < 1 || K > 4096 || !(eps > 0) ||
         tail_degree < -1 || tail_degree > 1)
         return MF_E_INVAL;
-    if (rbf != MF_RBF_GAUSSIAN) return MF_E_NOTIMPL;
+    if (rbf < MF_RBF_GAUSSIAN || rbf > MF_RBF_IMQ) return MF_E_INVAL;
+    if (tail_degree < mf::rbf_min_tail(rbf)) return MF_E_INVAL;   // no unique interpolant
+    if (N <= (tail_degree < 0 ? 0 : tail_degree == 0 ? 1 : 5)) return MF_E_INVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -362,6 +368,7 @@ int mf_build(const double *nodes, const double *node_values, int N, int K, mf_rb
     h->N = N;
     h->K = K;
     h->eps = eps;
+    h->rbf = rbf;
     h->tail_degree = tail_degree;
     h->P = tail_degree < 0 ? 0 : (tail_degree == 0 ? 1 : 5);
     h->nodes_h.assign(nodes, nodes + (size_t)N * 4);
@@ -597,6 +604,11 @@ int mf_set_option(mf_handle *h, const char *key, double value) {
         h->tc_pair = (int)value;
         return MF_OK;
     }
+    if (k == "tc_chunk") {   // passes per cluster launch at most (0: as many as fit)
+        if (value < 0 || value > 8 || value != (int)value || value == 1) return MF_E_INVAL;
+        h->tc_chunk = (int)value;
+        return MF_OK;
+    }
     if (k == "tc_nbs") {
         int v = (int)value;
         if (v != 0 && (v < 2 || v > 6)) return MF_E_INVAL;
@@ -640,6 +652,7 @@ int mf_query(const mf_handle *h, const char *key, double *value) {
     else if (k == "Kdev") *value = h->Kdev;
     else if (k == "form") *value = (double)h->form;
     else if (k == "tc_design") *value = h->tc_tmem ? 1.0 : 0.0;
+    else if (k == "tc_paired") *value = h->tc_paired;
     else if (k == "launches" && h->form == MF_FORM_MLP)
         return mf::surrogate_query(h, k, value);
     else if (k == "launches")

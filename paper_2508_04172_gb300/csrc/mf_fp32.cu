@@ -91,7 +91,8 @@ __device__ __forceinline__ void fp32_tile(const float *__restrict__ intr, const 
             float4 v = *reinterpret_cast<const float4 *>(W + (size_t)(n0 + r) * Kdev + ps.col0 + 4 * c4);
             *reinterpret_cast<float4 *>(w_s + r * width + 4 * c4) = v;
         }
-        // RBF values exp(-eps^2 |x - y|^2) = exp2(-|pre (x - y)|^2), tail monomials
+        // RBF values (Gaussian exp(-eps^2 |x - y|^2) = exp2(-|pre (x - y)|^2),
+        // other kernels phi(s^2 = |pre (x - y)|^2)), tail monomials
         {
             float4 xs = xs_s[wq];
             float4 xu = xu_s[wq];
@@ -106,7 +107,7 @@ __device__ __forceinline__ void fp32_tile(const float *__restrict__ intr, const 
                     r2 = fmaf(d1, d1, r2);
                     r2 = fmaf(d2, d2, r2);
                     r2 = fmaf(d3, d3, r2);
-                    v = exp2f(-r2);
+                    v = rot.rbf == 0 ? exp2f(-r2) : rbf_other(rot.rbf, r2);
                 } else {
                     int p = n - N;
                     v = (p == 0) ? 1.f : (p == 1) ? xu.x : (p == 2) ? xu.y : (p == 3) ? xu.z

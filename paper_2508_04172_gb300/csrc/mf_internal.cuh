@@ -6,6 +6,7 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <cmath>
 #include <vector>
 #include <string>
 
@@ -72,8 +73,20 @@ struct EpiParams {
 struct RotParams {
     float R[16];
     float centre[4];
-    float pre;               // eps * sqrt(log2 e): exp(-(eps r)^2) = exp2(-|pre (x - y)|^2)
+    float pre;               // Gaussian: eps * sqrt(log2 e), exp(-(eps r)^2) = exp2(-|pre (x - y)|^2);
+                             // other kernels: eps, s^2 = |pre (x - y)|^2
+    int rbf;                 // mf_rbf
 };
+
+// phi at s2 = (eps r)^2 for the kernels other than the Gaussian (mf_rbf):
+// PHS3 s^3, MQ sqrt(1 + s^2), IMQ 1 / sqrt(1 + s^2)
+__device__ __forceinline__ float rbf_other(int kind, float s2) {
+    return kind == 1 ? s2 * sqrtf(s2) : kind == 2 ? sqrtf(1.f + s2) : rsqrtf(1.f + s2);
+}
+// phi at s2 = (eps r)^2 in FP64, every kernel (start-up and labels)
+__device__ __forceinline__ double rbf_phi64(int kind, double s2) {
+    return kind == 0 ? exp(-s2) : kind == 1 ? s2 * sqrt(s2) : kind == 2 ? sqrt(1.0 + s2) : 1.0 / sqrt(1.0 + s2);
+}
 
 // One interpolant as the tcgen05 kernel sees it: everything that does not
 // change from call to call.  Passed by value (one event) or as a device
@@ -174,6 +187,8 @@ struct mf_handle {
     alignas(64) unsigned char tmap_lo2[128];
     bool pair_ok = false;           // the half-height maps exist
     int tc_pair = 1;                // 1: pair two query tiles per cluster when possible, 0: never
+    int tc_chunk = 0;               // passes per cluster launch at most (0: as many as fit)
+    int tc_paired = 0;              // the last cluster launch paired two query tiles
     int nbox = 0;                   // rows (device columns) per W tile = widest pass
     // scratch
     unsigned long long *d_bad = nullptr;
@@ -185,6 +200,14 @@ struct mf_handle {
 };
 
 namespace mf {
+// Smallest tail degree giving a unique interpolant for the kernel (the rule
+// after Eq. rbfcoeff: conditionally positive definite of order r needs the
+// monomials of degree r - 1): PHS3 order 2, MQ order 1, Gaussian / IMQ none.
+inline int rbf_min_tail(int rbf) { return rbf == MF_RBF_PHS3 ? 1 : rbf == MF_RBF_MQ ? 0 : -1; }
+// Node / query prescale: the Gaussian folds log2 e in (the kernels use exp2).
+inline double rbf_prescale(const mf_handle *h) {
+    return h->rbf == MF_RBF_GAUSSIAN ? h->eps * std::sqrt(1.0 / std::log(2.0)) : h->eps;
+}
 int cuda_status(cudaError_t e);
 // Diagnostics to stderr when the environment variable MF_LOG is set.
 void log_msg(const char *fmt, ...);
@@ -207,9 +230,13 @@ int launch_combine(const float *partial, int n_pass, int Q, float *out, cudaStre
 int launch_tc2(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
                cudaStream_t st, float *partial, float *cols = nullptr);
 int tc2_pass_max();
+// C[m][n] = A[m][k] B[k][n], row-major FP64 (stream-ordered)
+int dgemm_rm(int m, int n, int k, const double *A, int lda, const double *B, int ldb, double *C, int ldc,
+             cudaStream_t st);
 // batched tcgen05 launch (all events share form and mode count)
 int fill_tc_event(const mf_handle *h, TcEvent *out);
 size_t tc_smem_bytes(mf_form f, int np, int nbox_max, int sb);   // 0: does not fit
+int tc_max_passes(mf_form f, int nbox);   // passes one cluster launch stages
 int tc_batch_max_clusters(mf_form f, int n_modes, int np, int nbox_max, int sb, int *max_clusters);
 int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBatchCall &bc,
                     cudaStream_t st);

@@ -540,8 +540,6 @@ int mf_mlp_query(const mf_mlp *m, const char *key, double *value) {
 // held-out gate fails, and for queries outside the training radius.
 // ===================================================================
 
-#include <cublas_v2.h>
-
 struct mf_surrogate {
     mf_mlp *net = nullptr;
     int K = 0, K_out = 0;                 // user columns, network outputs (K rounded to 8)
@@ -596,10 +594,11 @@ __global__ void sur_rotate_kernel(const float *__restrict__ th, int n, const dou
     rad[i] = (float)sqrt(r2);
 }
 
-// Augmented RBF row of every point (Eq. rbfcoeff): exp(-eps^2 |x - y_n|^2)
-// for the N nodes, then the tail monomials 1, x_1..x_4 (first P of them).
+// Augmented RBF row of every point (Eq. rbfcoeff): phi(eps |x - y_n|) for
+// the N nodes (kernel `kind`, mf_rbf), then the tail monomials 1, x_1..x_4
+// (first P of them).
 __global__ void sur_phi_kernel(const double *__restrict__ x, int rows, const double *__restrict__ nodes, int N,
-                               int P, double eps2, double *__restrict__ phi) {
+                               int P, double eps2, int kind, double *__restrict__ phi) {
     const int NP = N + P;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)rows * NP;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -610,7 +609,7 @@ __global__ void sur_phi_kernel(const double *__restrict__ x, int rows, const dou
             const double *y = nodes + (size_t)n * 4;
             double r2 = 0.0;
             for (int k = 0; k < 4; ++k) r2 += (xi[k] - y[k]) * (xi[k] - y[k]);
-            v = exp(-eps2 * r2);
+            v = rbf_phi64(kind, eps2 * r2);
         } else {
             const int q = n - N;
             v = q == 0 ? 1.0 : xi[q - 1];
@@ -1073,20 +1072,13 @@ int mf_train_surrogate(mf_handle *h, const float *train_intrinsic, int n_train, 
     memcpy(Rh + 16, h->centre, 4 * sizeof(double));
     cudaMemcpy(Rc, Rh, sizeof(Rh), cudaMemcpyHostToDevice);
     mf::sur_rotate_kernel<<<(n_train + 255) / 256, 256, 0, st>>>(train_intrinsic, n_train, Rc, x64, x32, rad);
-    cublasHandle_t cb = nullptr;
-    if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) { cleanup(); mf::free_surrogate(h); return MF_E_CUDA; }
-    cublasSetStream(cb, st);
-    const double one = 1.0, zero = 0.0;
     for (int r0 = 0; r0 < n_train && rc == MF_OK; r0 += lrows) {
         const int rows = std::min(lrows, n_train - r0);
         mf::sur_phi_kernel<<<1024, 256, 0, st>>>(x64 + (size_t)r0 * 4, rows, h->d_nodes64, h->N, h->P,
-                                                 h->eps * h->eps, phi);
-        // row-major F[rows][K] = Phi[rows][NP] W[NP][K]  (column-major: F^T = W^T Phi^T)
-        if (cublasDgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, K, rows, NP, &one, h->d_W64, K, phi, NP, &zero,
-                        F + (size_t)r0 * K, K) != CUBLAS_STATUS_SUCCESS)
-            rc = MF_E_CUDA;
+                                                 h->eps * h->eps, (int)h->rbf, phi);
+        // F[rows][K] = Phi[rows][NP] W[NP][K]
+        rc = mf::dgemm_rm(rows, K, NP, phi, NP, h->d_W64, K, F + (size_t)r0 * K, K, st);
     }
-    cublasDestroy(cb);
     if (rc) { cleanup(); mf::free_surrogate(h); return rc; }
     mf::sur_colstats_kernel<<<K, 256, 0, st>>>(F, n_train, K, s->d_mu, s->d_s);
     mf::sur_floor_scale_kernel<<<1, 1, 0, st>>>(s->d_s, K);

@@ -1,20 +1,20 @@
 // Start-up stage on the GPU in FP64 (not part of the per-query path):
-//   * RBF interpolant construction, Eq. (rbfcoeff): Cholesky of the Gaussian
-//     matrix Phi, the tail handled through the Schur complement
-//     (P^T Phi^-1 P) b = P^T Phi^-1 F, a = Phi^-1 (F - P b)  (so P^T a = 0),
-//     plus power / inverse iteration for cond(Phi) and a cancellation probe.
-//   * SVD compression of an overlap matrix, Eq. (SVD): dense FP64 SVD of the
-//     node-by-time matrix, projection C = Z V.
+//   * RBF interpolant construction, Eq. (rbfcoeff).  Positive definite kernels
+//     (Gaussian, IMQ): Cholesky of Phi, the tail handled through the Schur
+//     complement (P^T Phi^-1 P) b = P^T Phi^-1 F, a = Phi^-1 (F - P b) (so
+//     P^T a = 0).  Conditionally definite kernels (PHS3 of order 2, MQ of
+//     order 1, with a tail of at least the matching degree): the null-space
+//     method -- Householder Q R = P, a = Q [0; c] with
+//     (s Q2^T Phi Q2) c = s Q2^T F positive definite (s = -1 for MQ), then
+//     R b = Q1^T (F - Phi a).  Power / inverse iteration give the condition
+//     number of the matrix factored; a cancellation probe follows.
 //   * 4x4 metric eigendecomposition (cyclic Jacobi) for the Delta-e rotation
 //     (Sec. II D) and the 10-sample not-a-knot spline operator (Sec. II D).
 // The Cholesky factorisation and triangular solves are this library's own
-// FP64 kernels (mf_chol.cu); the SVD uses cuSOLVER and its projection GEMM
-// cuBLAS; the matrix assembly, Schur step, iterations and small solves are
-// kernels here.
+// FP64 kernels (mf_chol.cu), as is the SVD compression of the overlap
+// matrices (mf_svd.cu); the matrix assembly, Schur step, iterations and
+// small solves are kernels here.
 #include "mf_internal.cuh"
-
-#include <cublas_v2.h>
-#include <cusolverDn.h>
 
 #include <algorithm>
 #include <cmath>
@@ -29,15 +29,6 @@ int chol_factor(double *A, int N, double *diag0, int *err, cudaStream_t st);
 int chol_solve(const double *L, int N, double *X, int ncols, cudaStream_t st);
 namespace {
 
-struct Libs {
-    cusolverDnHandle_t sol = nullptr;
-    cublasHandle_t blas = nullptr;
-    ~Libs() {
-        if (sol) cusolverDnDestroy(sol);
-        if (blas) cublasDestroy(blas);
-    }
-};
-
 template <class T>
 struct DevBuf {
     T *p = nullptr;
@@ -45,7 +36,7 @@ struct DevBuf {
     cudaError_t alloc(size_t n) { return cudaMalloc((void **)&p, n * sizeof(T)); }
 };
 
-__global__ void assemble_phi64(const double *__restrict__ y, int N, double eps2,
+__global__ void assemble_phi64(const double *__restrict__ y, int N, double eps2, int kind,
                                double *__restrict__ A) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
@@ -56,7 +47,7 @@ __global__ void assemble_phi64(const double *__restrict__ y, int N, double eps2,
         double t = y[i * 4 + d] - y[j * 4 + d];
         r2 += t * t;
     }
-    A[(size_t)i * N + j] = exp(-eps2 * r2);
+    A[(size_t)i * N + j] = rbf_phi64(kind, eps2 * r2);
 }
 
 // B (column-major N x (K+P)): columns 0..K-1 = F^T rows, K.. = tail monomials.
@@ -176,7 +167,7 @@ __global__ void fill64(double *x, int N, double v) {
 
 // max over sampled nodes i and columns k of sum_n |a_nk| phi(y_i, y_n)
 __global__ void cancellation_probe(const double *__restrict__ y, const double *__restrict__ W,
-                                   int N, int K, double eps2, int stride,
+                                   int N, int K, double eps2, int kind, int stride,
                                    double *__restrict__ out) {
     int i = blockIdx.x * stride;
     if (i >= N) return;
@@ -190,7 +181,7 @@ __global__ void cancellation_probe(const double *__restrict__ y, const double *_
                 double t = y[i * 4 + d] - y[n * 4 + d];
                 r2 += t * t;
             }
-            acc += fabs(W[(size_t)n * K + k]) * exp(-eps2 * r2);
+            acc += fabs(W[(size_t)n * K + k]) * fabs(rbf_phi64(kind, eps2 * r2));
         }
         best = fmax(best, acc);
     }
@@ -202,6 +193,151 @@ __global__ void cancellation_probe(const double *__restrict__ y, const double *_
         __syncthreads();
     }
     if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+// ------------------------------------------ null-space method (PHS3, MQ)
+// Householder QR of the tail matrix P [N][np] (monomials 1, y_1..y_4 of the
+// nodes), one CTA: P = H_0 .. H_{np-1} [R; 0], H_c = I - tau_c v_c v_c^T,
+// v_c zero above row c.  Pw [np][N] workspace; V [np][N]; R [np][np].
+__device__ double block_sum64(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    return s;
+}
+
+__global__ void __launch_bounds__(1024) tail_qr(const double *__restrict__ y, int N, int np,
+                                                double *__restrict__ Pw, double *__restrict__ V,
+                                                double *__restrict__ tau, double *__restrict__ R) {
+    __shared__ double red[32];
+    for (int i = threadIdx.x; i < N; i += blockDim.x)
+        for (int p = 0; p < np; ++p) Pw[(size_t)p * N + i] = p == 0 ? 1.0 : y[i * 4 + p - 1];
+    for (int i = threadIdx.x; i < np * np; i += blockDim.x) R[i] = 0.0;
+    __syncthreads();
+    for (int c = 0; c < np; ++c) {
+        double *x = Pw + (size_t)c * N, *v = V + (size_t)c * N;
+        double s = 0.0;
+        for (int i = c + threadIdx.x; i < N; i += blockDim.x) s += x[i] * x[i];
+        const double nrm = sqrt(block_sum64(s, red));
+        const double x0 = x[c];
+        const double alpha = x0 >= 0.0 ? -nrm : nrm;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) v[i] = i < c ? 0.0 : (i == c ? x0 - alpha : x[i]);
+        __syncthreads();
+        double t = 0.0;
+        for (int i = c + threadIdx.x; i < N; i += blockDim.x) t += v[i] * v[i];
+        const double vtv = block_sum64(t, red);
+        const double tc = vtv > 0.0 ? 2.0 / vtv : 0.0;
+        if (threadIdx.x == 0) {
+            tau[c] = tc;
+            R[c * np + c] = alpha;
+        }
+        for (int j = c + 1; j < np; ++j) {
+            double *z = Pw + (size_t)j * N;
+            double d = 0.0;
+            for (int i = c + threadIdx.x; i < N; i += blockDim.x) d += v[i] * z[i];
+            d = block_sum64(d, red) * tc;
+            for (int i = c + threadIdx.x; i < N; i += blockDim.x) z[i] -= d * v[i];
+            __syncthreads();
+            if (threadIdx.x == 0) R[c * np + j] = z[c];
+        }
+        __syncthreads();
+    }
+}
+
+// out = v . w (one CTA)
+__global__ void dot64(const double *__restrict__ v, const double *__restrict__ w, int N, double *__restrict__ out) {
+    __shared__ double red[32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += v[i] * w[i];
+    s = block_sum64(s, red);
+    if (threadIdx.x == 0) *out = s;
+}
+
+// X <- H X H for symmetric X [N][N], H = I - tau v v^T, given w = X v and
+// c = v . w:  X - tau (v w^T + w v^T) + tau^2 c v v^T
+__global__ void sym_reflect(double *__restrict__ X, int N, const double *__restrict__ v, const double *__restrict__ w,
+                            const double *__restrict__ tau, const double *__restrict__ c) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= N) return;
+    const double t = *tau;
+    X[(size_t)i * N + j] += -t * (v[i] * w[j] + w[i] * v[j]) + t * t * (*c) * v[i] * v[j];
+}
+
+// G <- H G for the K columns of G (column-major, column k at G + k N); one
+// CTA per column
+__global__ void reflect_cols(double *__restrict__ G, int N, const double *__restrict__ v,
+                             const double *__restrict__ tau) {
+    __shared__ double red[32];
+    double *g = G + (size_t)blockIdx.x * N;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) s += v[i] * g[i];
+    const double u = block_sum64(s, red) * (*tau);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) g[i] -= u * v[i];
+}
+
+// B [n2][n2] = sgn * X[np:, np:]   (X [N][N] row-major)
+__global__ void extract_block(const double *__restrict__ X, int N, int np, double sgn, double *__restrict__ B) {
+    const int n2 = N - np;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.y;
+    if (j >= n2) return;
+    B[(size_t)i * n2 + j] = sgn * X[(size_t)(i + np) * N + np + j];
+}
+
+// C [K][n2] (column-major) = sgn * G[np:, :]   (G column-major N x K)
+__global__ void extract_rows(const double *__restrict__ G, int N, int np, double sgn, double *__restrict__ C) {
+    const int n2 = N - np;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= n2) return;
+    C[(size_t)k * n2 + i] = sgn * G[(size_t)k * N + np + i];
+}
+
+// A [K][N] (column-major) = [0 (np rows); C]
+__global__ void embed_rows(const double *__restrict__ C, int N, int np, double *__restrict__ A) {
+    const int n2 = N - np;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.y;
+    if (i >= N) return;
+    A[(size_t)k * N + i] = i < np ? 0.0 : C[(size_t)k * n2 + i - np];
+}
+
+// T[p][k] = G[k][p] - sum_j X[p][np + j] C[k][j]   (p < np; one CTA per (k, p))
+__global__ void tail_rhs(const double *__restrict__ X, const double *__restrict__ G, const double *__restrict__ C,
+                         int N, int np, int K, double *__restrict__ T) {
+    __shared__ double red[32];
+    const int k = blockIdx.x, p = blockIdx.y;
+    const int n2 = N - np;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n2; j += blockDim.x) s += X[(size_t)p * N + np + j] * C[(size_t)k * n2 + j];
+    s = block_sum64(s, red);
+    if (threadIdx.x == 0) T[(size_t)p * K + k] = G[(size_t)k * N + p] - s;
+}
+
+// b = R^-1 T (R upper triangular np x np), column by column; W rows:
+// W[n][k] = A[k][n] (n < N), W[N + p][k] = b[p][k]
+__global__ void tail_back_solve(const double *__restrict__ R, int np, const double *__restrict__ T, int K,
+                                double *__restrict__ W, int N) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    double b[5];
+    for (int r = np - 1; r >= 0; --r) {
+        double acc = T[(size_t)r * K + k];
+        for (int c = r + 1; c < np; ++c) acc -= R[r * np + c] * b[c];
+        b[r] = acc / R[r * np + r];
+        W[(size_t)(N + r) * K + k] = b[r];
+    }
+}
+
+__global__ void transpose_weights(const double *__restrict__ A, int N, int K, double *__restrict__ W) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (k >= K) return;
+    W[(size_t)n * K + k] = A[(size_t)k * N + n];
 }
 
 __global__ void absmax64(const double *__restrict__ x, size_t n, double *__restrict__ out) {
@@ -308,20 +444,6 @@ __global__ void spline_operator(double *__restrict__ G45) {
 }
 
 // SVD helpers: Zc = column-major copy of Z (N x M); basis rows from V^H.
-__global__ void transpose_z(const cuDoubleComplex *__restrict__ Z, int N, int M,
-                            cuDoubleComplex *__restrict__ Zc) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int n = blockIdx.y;
-    if (t < M) Zc[(size_t)t * N + n] = Z[(size_t)n * M + t];
-}
-
-__global__ void pick_basis(const cuDoubleComplex *__restrict__ VT, int M, int rank,
-                           cuDoubleComplex *__restrict__ Vsel) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int i = blockIdx.y;
-    if (t < M) Vsel[(size_t)i * M + t] = VT[(size_t)t * M + i];
-}
-
 // Cubic coefficients of the 10-sample not-a-knot spline on [j, j+1]:
 //   S(u) = y4 + u (y5 - y4 - m4/3 - m5/6) + u^2 m4/2 + u^3 (m5 - m4)/6,
 // m4, m5 = knot second derivatives (rows 4, 5 of the spline operator) of the
@@ -410,67 +532,67 @@ int compute_stencil(mf_handle *h) {
     return MF_OK;
 }
 
-int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
-    const int N = h->N, K = h->K, P = h->P;
-    const int ncols = K + P;
-    DevBuf<double> A, B, F, T, b, x, y, nrm, cancel, fmax_d, diag0;
-    DevBuf<int> err, cerr;
-    MF_CUDA(A.alloc((size_t)N * N));
-    MF_CUDA(B.alloc((size_t)N * ncols));
-    MF_CUDA(F.alloc((size_t)N * K));
-    MF_CUDA(T.alloc((size_t)5 * ncols));
-    MF_CUDA(b.alloc((size_t)(P > 0 ? P : 1) * K));
-    MF_CUDA(x.alloc(N));
-    MF_CUDA(y.alloc(N));
+// Largest eigenvalue (power iteration), Cholesky factor in place, smallest
+// eigenvalue (inverse iteration with the factor) of the SPD matrix A [n][n].
+// MF_E_ILLCOND when a pivot is not positive beyond rounding.
+static int factor_estimate(double *A, int n, double *lmax_out, double *lmin_out, cudaStream_t st) {
+    DevBuf<double> x, y, nrm, diag0;
+    DevBuf<int> cerr;
+    MF_CUDA(x.alloc(n));
+    MF_CUDA(y.alloc(n));
     MF_CUDA(nrm.alloc(1));
-    MF_CUDA(err.alloc(1));
+    MF_CUDA(diag0.alloc(n));
     MF_CUDA(cerr.alloc(1));
-    MF_CUDA(fmax_d.alloc(1));
-    MF_CUDA(diag0.alloc(N));
-    MF_CUDA(cudaMemcpyAsync(F.p, F_host, sizeof(double) * (size_t)N * K, cudaMemcpyHostToDevice, st));
-    MF_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
     MF_CUDA(cudaMemsetAsync(cerr.p, 0, sizeof(int), st));
-
-    const double eps2 = h->eps * h->eps;
-    assemble_phi64<<<dim3((N + 255) / 256, N), 256, 0, st>>>(h->d_nodes64, N, eps2, A.p);
-    MF_CUDA(cudaGetLastError());
-    // lambda_max by power iteration (before the factorization overwrites Phi)
-    fill64<<<(N + 255) / 256, 256, 0, st>>>(x.p, N, 1.0 / std::sqrt((double)N));
+    fill64<<<(n + 255) / 256, 256, 0, st>>>(x.p, n, 1.0 / std::sqrt((double)n));
     double lmax = 0.0;
     for (int it = 0; it < 60; ++it) {
-        matvec64<<<(N + 7) / 8, 256, 0, st>>>(A.p, x.p, N, y.p);
-        normalize64<<<1, 256, 0, st>>>(y.p, N, x.p, nrm.p);
+        matvec64<<<(n + 7) / 8, 256, 0, st>>>(A, x.p, n, y.p);
+        normalize64<<<1, 256, 0, st>>>(y.p, n, x.p, nrm.p);
     }
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaMemcpyAsync(&lmax, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
-
-    // Phi = L L^T (FP64, blocked right-looking); a pivot that is not positive
-    // beyond rounding means Phi is numerically singular
-    int rc = chol_factor(A.p, N, diag0.p, cerr.p, st);
+    // A = L L^T (FP64, blocked right-looking)
+    int rc = chol_factor(A, n, diag0.p, cerr.p, st);
     if (rc) return rc;
     int hc = 0;
     MF_CUDA(cudaMemcpyAsync(&hc, cerr.p, sizeof(int), cudaMemcpyDeviceToHost, st));
     MF_CUDA(cudaStreamSynchronize(st));
     if (hc != 0) return MF_E_ILLCOND;
-
-    // lambda_min by inverse iteration with the Cholesky factor
-    fill64<<<(N + 255) / 256, 256, 0, st>>>(x.p, N, 1.0 / std::sqrt((double)N));
+    fill64<<<(n + 255) / 256, 256, 0, st>>>(x.p, n, 1.0 / std::sqrt((double)n));
     double inv = 0.0;
     for (int it = 0; it < 40; ++it) {
-        MF_CUDA(cudaMemcpyAsync(y.p, x.p, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
-        rc = chol_solve(A.p, N, y.p, 1, st);
+        MF_CUDA(cudaMemcpyAsync(y.p, x.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        rc = chol_solve(A, n, y.p, 1, st);
         if (rc) return rc;
-        normalize64<<<1, 256, 0, st>>>(y.p, N, x.p, nrm.p);
+        normalize64<<<1, 256, 0, st>>>(y.p, n, x.p, nrm.p);
     }
     MF_CUDA(cudaGetLastError());
     MF_CUDA(cudaMemcpyAsync(&inv, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    *lmax_out = lmax;
+    *lmin_out = (inv > 0) ? 1.0 / inv : 0.0;
+    return MF_OK;
+}
 
-    // solve Phi X = [F | P]
-    assemble_rhs<<<dim3((N + 255) / 256, ncols), 256, 0, st>>>(F.p, h->d_nodes64, N, K, P, B.p);
-    MF_CUDA(cudaGetLastError());
-    rc = chol_solve(A.p, N, B.p, ncols, st);
+// Positive definite kernels: Cholesky of Phi and the tail's Schur complement.
+static int rbf_build_pd(mf_handle *h, double *A, const double *F, cudaStream_t st, double *lmax, double *lmin) {
+    const int N = h->N, K = h->K, P = h->P;
+    const int ncols = K + P;
+    DevBuf<double> B, T, b;
+    DevBuf<int> err;
+    MF_CUDA(B.alloc((size_t)N * ncols));
+    MF_CUDA(T.alloc((size_t)5 * ncols));
+    MF_CUDA(b.alloc((size_t)(P > 0 ? P : 1) * K));
+    MF_CUDA(err.alloc(1));
+    MF_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), st));
+    int rc = factor_estimate(A, N, lmax, lmin, st);
     if (rc) return rc;
-    MF_CUDA(cudaMalloc((void **)&h->d_W64, sizeof(double) * (size_t)(N + P) * K));
+    // solve Phi X = [F | P]
+    assemble_rhs<<<dim3((N + 255) / 256, ncols), 256, 0, st>>>(F, h->d_nodes64, N, K, P, B.p);
+    MF_CUDA(cudaGetLastError());
+    rc = chol_solve(A, N, B.p, ncols, st);
+    if (rc) return rc;
     if (P > 0) {
         tail_dots<<<ncols, 256, 0, st>>>(B.p, h->d_nodes64, N, P, T.p, ncols);
         solve_tail<<<(K + 127) / 128, 128, 0, st>>>(T.p, K, P, ncols, b.p, err.p);
@@ -480,13 +602,91 @@ int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
     MF_CUDA(cudaGetLastError());
     int herr = 0;
     MF_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    return herr ? MF_E_ILLCOND : MF_OK;
+}
+
+// Conditionally definite kernels (PHS3: s = +1, MQ: s = -1): the null-space
+// method.  With Q R = P (Householder) and a = Q [0; c], the saddle system
+// becomes (s X22) c = s G2 and R b = G1 - X12 c, where X = Q^T Phi Q and
+// G = Q^T F; s X22 is positive definite for a kernel of order <= tail
+// degree + 1 (Micchelli).
+static int rbf_build_cpd(mf_handle *h, double *A, const double *F, cudaStream_t st, double *lmax, double *lmin) {
+    const int N = h->N, K = h->K, np = h->P, n2 = N - np;
+    const double sgn = h->rbf == MF_RBF_MQ ? -1.0 : 1.0;
+    DevBuf<double> Pw, V, tau, R, w, c, B2, G, C2, Af, T;
+    MF_CUDA(Pw.alloc((size_t)np * N));
+    MF_CUDA(V.alloc((size_t)np * N));
+    MF_CUDA(tau.alloc(np));
+    MF_CUDA(R.alloc((size_t)np * np));
+    MF_CUDA(w.alloc(N));
+    MF_CUDA(c.alloc(1));
+    MF_CUDA(B2.alloc((size_t)n2 * n2));
+    MF_CUDA(G.alloc((size_t)N * K));
+    MF_CUDA(C2.alloc((size_t)n2 * K));
+    MF_CUDA(Af.alloc((size_t)N * K));
+    MF_CUDA(T.alloc((size_t)np * K));
+    tail_qr<<<1, 1024, 0, st>>>(h->d_nodes64, N, np, Pw.p, V.p, tau.p, R.p);
+    MF_CUDA(cudaGetLastError());
+    std::vector<double> Rh((size_t)np * np);
+    MF_CUDA(cudaMemcpyAsync(Rh.data(), R.p, sizeof(double) * np * np, cudaMemcpyDeviceToHost, st));
+    MF_CUDA(cudaStreamSynchronize(st));
+    double rmax = 0.0;
+    for (int i = 0; i < np; ++i) rmax = std::max(rmax, std::fabs(Rh[i * np + i]));
+    for (int i = 0; i < np; ++i)
+        if (!(std::fabs(Rh[i * np + i]) > 1e-12 * rmax)) return MF_E_ILLCOND;   // the tail is not unisolvent
+    // X = Q^T Phi Q, one reflector at a time
+    for (int i = 0; i < np; ++i) {
+        const double *v = V.p + (size_t)i * N;
+        matvec64<<<(N + 7) / 8, 256, 0, st>>>(A, v, N, w.p);
+        dot64<<<1, 256, 0, st>>>(v, w.p, N, c.p);
+        sym_reflect<<<dim3((N + 255) / 256, N), 256, 0, st>>>(A, N, v, w.p, tau.p + i, c.p);
+    }
+    extract_block<<<dim3((n2 + 255) / 256, n2), 256, 0, st>>>(A, N, np, sgn, B2.p);
+    MF_CUDA(cudaGetLastError());
+    int rc = factor_estimate(B2.p, n2, lmax, lmin, st);
+    if (rc) return rc;
+    // G = Q^T F (column-major N x K)
+    assemble_rhs<<<dim3((N + 255) / 256, K), 256, 0, st>>>(F, h->d_nodes64, N, K, 0, G.p);
+    for (int i = 0; i < np; ++i) reflect_cols<<<K, 256, 0, st>>>(G.p, N, V.p + (size_t)i * N, tau.p + i);
+    extract_rows<<<dim3((n2 + 255) / 256, K), 256, 0, st>>>(G.p, N, np, sgn, C2.p);
+    MF_CUDA(cudaGetLastError());
+    rc = chol_solve(B2.p, n2, C2.p, K, st);
+    if (rc) return rc;
+    // a = Q [0; c]
+    embed_rows<<<dim3((N + 255) / 256, K), 256, 0, st>>>(C2.p, N, np, Af.p);
+    for (int i = np - 1; i >= 0; --i) reflect_cols<<<K, 256, 0, st>>>(Af.p, N, V.p + (size_t)i * N, tau.p + i);
+    // R b = G1 - X12 c
+    tail_rhs<<<dim3(K, np), 256, 0, st>>>(A, G.p, C2.p, N, np, K, T.p);
+    transpose_weights<<<dim3((K + 127) / 128, N), 128, 0, st>>>(Af.p, N, K, h->d_W64);
+    tail_back_solve<<<(K + 127) / 128, 128, 0, st>>>(R.p, np, T.p, K, h->d_W64, N);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaStreamSynchronize(st));
+    return MF_OK;
+}
+
+int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
+    const int N = h->N, K = h->K, P = h->P;
+    const int kind = (int)h->rbf;
+    DevBuf<double> A, F, cancel, fmax_d;
+    MF_CUDA(A.alloc((size_t)N * N));
+    MF_CUDA(F.alloc((size_t)N * K));
+    MF_CUDA(fmax_d.alloc(1));
+    MF_CUDA(cudaMemcpyAsync(F.p, F_host, sizeof(double) * (size_t)N * K, cudaMemcpyHostToDevice, st));
+    const double eps2 = h->eps * h->eps;
+    assemble_phi64<<<dim3((N + 255) / 256, N), 256, 0, st>>>(h->d_nodes64, N, eps2, kind, A.p);
+    MF_CUDA(cudaGetLastError());
+    MF_CUDA(cudaMalloc((void **)&h->d_W64, sizeof(double) * (size_t)(N + P) * K));
+    double lmax = 0.0, lmin = 0.0;
+    const bool pd = h->rbf == MF_RBF_GAUSSIAN || h->rbf == MF_RBF_IMQ;
+    int rc = pd ? rbf_build_pd(h, A.p, F.p, st, &lmax, &lmin) : rbf_build_cpd(h, A.p, F.p, st, &lmax, &lmin);
+    if (rc) return rc;
 
     // cancellation probe on up to 16 nodes
     const int stride = std::max(1, N / 16);
     const int nprobe = (N + stride - 1) / stride;
     MF_CUDA(cancel.alloc(nprobe));
-    cancellation_probe<<<nprobe, 256, 0, st>>>(h->d_nodes64, h->d_W64, N, K, eps2, stride,
-                                               cancel.p);
+    cancellation_probe<<<nprobe, 256, 0, st>>>(h->d_nodes64, h->d_W64, N, K, eps2, kind, stride, cancel.p);
     absmax64<<<1, 256, 0, st>>>(F.p, (size_t)N * K, fmax_d.p);
     MF_CUDA(cudaGetLastError());
     std::vector<double> can(nprobe);
@@ -494,9 +694,8 @@ int rbf_build(mf_handle *h, const double *F_host, cudaStream_t st) {
     MF_CUDA(cudaMemcpyAsync(can.data(), cancel.p, sizeof(double) * nprobe, cudaMemcpyDeviceToHost, st));
     MF_CUDA(cudaMemcpyAsync(&fm, fmax_d.p, sizeof(double), cudaMemcpyDeviceToHost, st));
     MF_CUDA(cudaStreamSynchronize(st));
-    if (herr) return MF_E_ILLCOND;
     h->lam_max = lmax;
-    h->lam_min = (inv > 0) ? 1.0 / inv : 0.0;
+    h->lam_min = lmin;
     h->cond = (h->lam_min > 0) ? h->lam_max / h->lam_min : INFINITY;
     double cm = 0.0;
     for (double v : can) cm = std::max(cm, v);
@@ -518,52 +717,6 @@ int metric_eig(const double *metric, double *R_out) {
     for (int i = 0; i < 4; ++i)
         if (!(lam[i] > 0)) return MF_E_INVAL;   // metric must be positive definite
     return MF_OK;
-}
-
-int svd_compress(const double *z, int N, int M, int rank, double *coef, double *basis, double *sv,
-                 cudaStream_t st) {
-    if (N < M) return MF_E_INVAL;   // one row per node; more nodes than samples
-    Libs L;
-    MF_LIBCALL(cusolverDnCreate(&L.sol));
-    MF_LIBCALL(cublasCreate(&L.blas));
-    MF_LIBCALL(cusolverDnSetStream(L.sol, st));
-    MF_LIBCALL(cublasSetStream(L.blas, st));
-    DevBuf<cuDoubleComplex> Z, Zc, VT, Vsel, C, work;
-    DevBuf<double> S, rwork;
-    DevBuf<int> info;
-    MF_CUDA(Z.alloc((size_t)N * M));
-    MF_CUDA(Zc.alloc((size_t)N * M));
-    MF_CUDA(VT.alloc((size_t)M * M));
-    MF_CUDA(Vsel.alloc((size_t)rank * M));
-    MF_CUDA(C.alloc((size_t)N * rank));
-    MF_CUDA(S.alloc(M));
-    MF_CUDA(rwork.alloc(5 * (size_t)M));
-    MF_CUDA(info.alloc(1));
-    MF_CUDA(cudaMemcpyAsync(Z.p, z, sizeof(cuDoubleComplex) * (size_t)N * M, cudaMemcpyHostToDevice, st));
-    transpose_z<<<dim3((M + 255) / 256, N), 256, 0, st>>>(Z.p, N, M, Zc.p);
-    MF_CUDA(cudaGetLastError());
-    // Z = U S V^H (FP64 Householder bidiagonalisation + QR); only V^H is formed
-    int lwork = 0;
-    MF_LIBCALL(cusolverDnZgesvd_bufferSize(L.sol, N, M, &lwork));
-    MF_CUDA(work.alloc((size_t)lwork + 1));
-    signed char jobu = 'N', jobvt = 'A';
-    MF_LIBCALL(cusolverDnZgesvd(L.sol, jobu, jobvt, N, M, Zc.p, N, S.p, nullptr, 1, VT.p, M,
-                                work.p, lwork, rwork.p, info.p));
-    pick_basis<<<dim3((M + 255) / 256, rank), 256, 0, st>>>(VT.p, M, rank, Vsel.p);
-    MF_CUDA(cudaGetLastError());
-    // C[n][i] = sum_t Z[n][t] conj(u_i[t]):  column-major (rank x N) = U^H T, with
-    // T = Z^T (memory [N][M]) and U (M x rank) = basis rows stored [rank][M]
-    cuDoubleComplex a1 = make_cuDoubleComplex(1.0, 0.0), a0 = make_cuDoubleComplex(0.0, 0.0);
-    MF_LIBCALL(cublasZgemm(L.blas, CUBLAS_OP_C, CUBLAS_OP_N, rank, N, M, &a1, Vsel.p, M, Z.p, M,
-                           &a0, C.p, rank));
-    int hinfo = 0;
-    MF_CUDA(cudaMemcpyAsync(&hinfo, info.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-    MF_CUDA(cudaMemcpyAsync(coef, C.p, sizeof(cuDoubleComplex) * (size_t)N * rank, cudaMemcpyDeviceToHost, st));
-    MF_CUDA(cudaMemcpyAsync(basis, Vsel.p, sizeof(cuDoubleComplex) * (size_t)rank * M, cudaMemcpyDeviceToHost, st));
-    if (sv) MF_CUDA(cudaMemcpyAsync(sv, S.p, sizeof(double) * rank, cudaMemcpyDeviceToHost, st));
-    MF_CUDA(cudaStreamSynchronize(st));
-    if (hinfo != 0) log_msg("svd: gesvd info = %d (N = %d, M = %d)", hinfo, N, M);
-    return hinfo == 0 ? MF_OK : MF_E_CUDA;
 }
 
 }  // namespace mf

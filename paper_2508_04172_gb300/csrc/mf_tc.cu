@@ -385,6 +385,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
             const TcEvent &ev = src.event(e);
             const EvIO io = src.io(e);
             const int N = ev.N, P = ev.P, nkb = ev.nkb;
+            const int kind = ev.rot.rbf;
             const int rot = tile_rot(tile, nkb);
             float2 X[RPT / 2][4];   // row pairs (rg + 2h RS, rg + (2h+1) RS), per coordinate
             float4 xu[RPT];
@@ -429,19 +430,36 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                         const float4 y = scr[e8 * CPR + c];   // node c*8+e8 (conflict-free broadcast)
                         const float2 ny0 = make_float2(y.x, y.x), ny1 = make_float2(y.y, y.y);
                         const float2 ny2 = make_float2(y.z, y.z), ny3 = make_float2(y.w, y.w);
+                        if (kind == 0) {
 #pragma unroll
-                        for (int h2 = 0; h2 < RPT / 2; ++h2) {
-                            // r2 = |x - y|^2 - sc, so Phi * 2^sc = 2^-r2 (two rows at once)
-                            float2 dd = __fadd2_rn(X[h2][0], ny0);
-                            float2 r2 = __ffma2_rn(dd, dd, nsc);
-                            dd = __fadd2_rn(X[h2][1], ny1);
-                            r2 = __ffma2_rn(dd, dd, r2);
-                            dd = __fadd2_rn(X[h2][2], ny2);
-                            r2 = __ffma2_rn(dd, dd, r2);
-                            dd = __fadd2_rn(X[h2][3], ny3);
-                            r2 = __ffma2_rn(dd, dd, r2);
-                            v[2 * h2][e8] = ex2(-r2.x);
-                            v[2 * h2 + 1][e8] = ex2(-r2.y);
+                            for (int h2 = 0; h2 < RPT / 2; ++h2) {
+                                // r2 = |x - y|^2 - sc, so Phi * 2^sc = 2^-r2 (two rows at once)
+                                float2 dd = __fadd2_rn(X[h2][0], ny0);
+                                float2 r2 = __ffma2_rn(dd, dd, nsc);
+                                dd = __fadd2_rn(X[h2][1], ny1);
+                                r2 = __ffma2_rn(dd, dd, r2);
+                                dd = __fadd2_rn(X[h2][2], ny2);
+                                r2 = __ffma2_rn(dd, dd, r2);
+                                dd = __fadd2_rn(X[h2][3], ny3);
+                                r2 = __ffma2_rn(dd, dd, r2);
+                                v[2 * h2][e8] = ex2(-r2.x);
+                                v[2 * h2 + 1][e8] = ex2(-r2.y);
+                            }
+                        } else {
+#pragma unroll
+                            for (int h2 = 0; h2 < RPT / 2; ++h2) {
+                                // the other radial kernels: phi(s^2), s^2 = |pre (x - y)|^2
+                                float2 dd = __fadd2_rn(X[h2][0], ny0);
+                                float2 r2 = __fmul2_rn(dd, dd);
+                                dd = __fadd2_rn(X[h2][1], ny1);
+                                r2 = __ffma2_rn(dd, dd, r2);
+                                dd = __fadd2_rn(X[h2][2], ny2);
+                                r2 = __ffma2_rn(dd, dd, r2);
+                                dd = __fadd2_rn(X[h2][3], ny3);
+                                r2 = __ffma2_rn(dd, dd, r2);
+                                v[2 * h2][e8] = rbf_other(kind, r2.x) * tsc;
+                                v[2 * h2 + 1][e8] = rbf_other(kind, r2.y) * tsc;
+                            }
                         }
                     } else {
                         // tail monomials 1, x1..x4 (times 2^sc), then zero padding
@@ -846,22 +864,43 @@ int launch_tc_batch(mf_form f, int n_modes, const TcEvent *d_events, const TcBat
     return MF_OK;
 }
 
-// cols != nullptr: the columns-only variant, out [Q][K] (ext, out, partial unused).
-int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
-              cudaStream_t st, float *partial, float *cols) {
-    if (!h->d_Whi) return MF_E_STATE;
-    const int np = (int)h->passes.size();
-    if (np > kMaxCluster) return MF_E_NOTIMPL;
+// One launch over passes [p0, p0 + npc) of the handle (a cluster of npc, or
+// 2 npc when paired, CTAs per query tile); the pass partials go to rows
+// p0 .. p0 + npc - 1 of `partial`.
+static int launch_tc_part(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+                          cudaStream_t st, float *partial, float *cols, int p0, int npc) {
+    const int np = npc;
+    int sb = h->tc_nbs ? h->tc_nbs : 4;
+    while (!tc_smem_bytes(h->form, np, h->nbox, sb) && sb > 2) --sb;
+    const size_t smem = tc_smem_bytes(h->form, np, h->nbox, sb);
+    if (!smem) return MF_E_NOTIMPL;
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[1];
+    int rc;
     // paired launch: two query tiles per cluster sharing the weight tiles
-    // (cluster of 2 np <= 8 CTAs), for the 3-term lnL kernels
-    const bool pair = !cols && h->tc_pair && h->pair_ok && 2 * np <= kMaxCluster && form_terms(h->form) == 3 &&
-                      Q > kTile;
+    // (cluster of 2 np <= 8 CTAs), for the 3-term lnL kernels -- unless the
+    // larger clusters leave more than 7 % more SMs idle than the single
+    // launch's (clusters must fit a GPC; measured: pairing gains ~6 % at 6
+    // CTAs per cluster and loses ~20 % at 8)
+    bool pair = !cols && h->tc_pair && h->pair_ok && 2 * np <= kMaxCluster && form_terms(h->form) == 3 &&
+                Q > kTile;
+    if (pair) {
+        void *kp = pick_pair_kernel(h->form, h->n_modes), *ks = pick_kernel(h->form, h->n_modes, false);
+        int mp = 0, ms = 0;
+        if (!kp || !ks) return MF_E_NOTIMPL;
+        if ((rc = tc_config(kp, 2 * np, smem, st, cfg, attr, &mp))) return rc;
+        if ((rc = tc_config(ks, np, smem, st, cfg, attr, &ms))) return rc;
+        pair = 2.0 * np * mp >= 0.93 * np * ms;
+    }
+    h->tc_paired = pair ? 1 : 0;
     void *kern = cols ? pick_cols_kernel(h->form)
                       : pair ? pick_pair_kernel(h->form, h->n_modes) : pick_kernel(h->form, h->n_modes, false);
     if (!kern) return MF_E_NOTIMPL;
     TcEvent ev;
-    int rc = fill_tc_event(h, &ev);
+    rc = fill_tc_event(h, &ev);
     if (rc) return rc;
+    ev.epi.n_pass = np;
+    for (int i = 0; i < np; ++i) ev.epi.passes[i] = h->passes[p0 + i];
     TcCall c;
     memset(&c, 0, sizeof(c));
     c.cols = cols;
@@ -870,19 +909,14 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
     c.intr = intr;
     c.ext = ext;
     c.out = out;
-    c.partial = partial;
+    c.partial = partial ? partial + (size_t)p0 * Q : nullptr;
     c.Q = Q;
     c.E = E;
     c.n_tiles = (Q + kTile - 1) / kTile;
     c.n_items = pair ? (c.n_tiles + 1) / 2 : c.n_tiles;
     c.nbox_max = h->nbox;
     c.err = h->d_err;
-    c.sb = h->tc_nbs ? h->tc_nbs : 4;
-    while (!tc_smem_bytes(h->form, np, h->nbox, c.sb) && c.sb > 2) --c.sb;
-    const size_t smem = tc_smem_bytes(h->form, np, h->nbox, c.sb);
-    if (!smem) return MF_E_NOTIMPL;
-    cudaLaunchConfig_t cfg;
-    cudaLaunchAttribute attr[1];
+    c.sb = sb;
     int maxc = 0;
     const int cl = pair ? 2 * np : np;
     rc = tc_config(kern, cl, smem, st, cfg, attr, &maxc);
@@ -891,6 +925,36 @@ int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, f
     cfg.gridDim = dim3((unsigned)(c.n_clusters * cl), 1, 1);
     void *args[2] = {(void *)&ev, (void *)&c};
     MF_CUDA(cudaLaunchKernelExC(&cfg, kern, args));
+    return MF_OK;
+}
+
+int tc_max_passes(mf_form f, int nbox) {
+    for (int k = kMaxCluster; k >= 1; --k)
+        if (tc_smem_bytes(f, k, nbox, 2)) return k;
+    return 0;
+}
+
+// cols != nullptr: the columns-only variant, out [Q][K] (ext, out, partial unused).
+// More passes than one cluster stages (its shared memory holds one Phi slot
+// pair per pass) run as several launches over runs of 2 .. max passes, each
+// writing its own pass partials (the per-pass arithmetic, hence every
+// partial, is the same as in a single launch).
+int launch_tc(mf_handle *h, const float *intr, const float *ext, int Q, int E, float *out,
+              cudaStream_t st, float *partial, float *cols) {
+    if (!h->d_Whi) return MF_E_STATE;
+    const int np = (int)h->passes.size();
+    int maxnp = tc_max_passes(h->form, h->nbox);
+    if (h->tc_chunk > 0) maxnp = std::min(maxnp, h->tc_chunk);
+    if (maxnp < 1) return MF_E_NOTIMPL;
+    if (np <= maxnp) return launch_tc_part(h, intr, ext, Q, E, out, st, partial, cols, 0, np);
+    const int nch = (np + maxnp - 1) / maxnp;
+    if (np / nch < 2 || (!cols && !partial)) return MF_E_NOTIMPL;   // every run must write partials
+    for (int c = 0, p0 = 0; c < nch; ++c) {
+        const int cnt = np / nch + (c < np % nch ? 1 : 0);
+        const int rc = launch_tc_part(h, intr, ext, Q, E, out, st, partial, cols, p0, cnt);
+        if (rc) return rc;
+        p0 += cnt;
+    }
     return MF_OK;
 }
 

@@ -234,6 +234,7 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
                            ev.rot.R[4 * a + 3] * d3;
             }
             const float pre = ev.rot.pre;
+            const int kind = ev.rot.rbf;
             const float2 X0 = make_float2(x[0] * pre, x[0] * pre), X1 = make_float2(x[1] * pre, x[1] * pre);
             const float2 X2 = make_float2(x[2] * pre, x[2] * pre), X3 = make_float2(x[3] * pre, x[3] * pre);
             const int rot = tile_rot2(tile, nkb);
@@ -245,7 +246,7 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
                 __syncwarp();
                 const int n0 = (kb + rot < nkb ? kb + rot : kb + rot - nkb) * kKB + 16 * h;
                 float v[16];
-                if (n0 + 16 <= ev.N) {
+                if (n0 + 16 <= ev.N && kind == 0) {
 #pragma unroll
                     for (int j = 0; j < 16; j += 2) {
                         const float4 ya = buf[j], yb = buf[j + 1];   // pre-negated, pre-scaled
@@ -260,6 +261,22 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
                         v[j] = ex2(-r2.x);
                         v[j + 1] = ex2(-r2.y);
                     }
+                } else if (n0 + 16 <= ev.N) {
+                    // the other radial kernels, phi(s^2) with s^2 = |pre (x - y)|^2
+#pragma unroll
+                    for (int j = 0; j < 16; j += 2) {
+                        const float4 ya = buf[j], yb = buf[j + 1];
+                        float2 dd = __fadd2_rn(X0, make_float2(ya.x, yb.x));
+                        float2 r2 = __fmul2_rn(dd, dd);
+                        dd = __fadd2_rn(X1, make_float2(ya.y, yb.y));
+                        r2 = __ffma2_rn(dd, dd, r2);
+                        dd = __fadd2_rn(X2, make_float2(ya.z, yb.z));
+                        r2 = __ffma2_rn(dd, dd, r2);
+                        dd = __fadd2_rn(X3, make_float2(ya.w, yb.w));
+                        r2 = __ffma2_rn(dd, dd, r2);
+                        v[j] = rbf_other(kind, r2.x) * tsc;
+                        v[j + 1] = rbf_other(kind, r2.y) * tsc;
+                    }
                 } else {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
@@ -267,11 +284,11 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
                         if (n < ev.N) {
                             const float4 y = buf[j];
                             const float e0 = X0.x + y.x, e1 = X1.x + y.y, e2 = X2.x + y.z, e3 = X3.x + y.w;
-                            float r2 = fmaf(e0, e0, -kPhiLog2);
+                            float r2 = fmaf(e0, e0, kind == 0 ? -kPhiLog2 : 0.f);
                             r2 = fmaf(e1, e1, r2);
                             r2 = fmaf(e2, e2, r2);
                             r2 = fmaf(e3, e3, r2);
-                            v[j] = ex2(-r2);
+                            v[j] = kind == 0 ? ex2(-r2) : rbf_other(kind, r2) * tsc;
                         } else {
                             const int q = n - ev.N;      // tail monomials 1, x1..x4, then padding
                             const float m = (q == 0) ? 1.f : (q == 1) ? x[0] : (q == 2) ? x[1] : (q == 3) ? x[2] : x[3];

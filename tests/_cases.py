@@ -35,7 +35,8 @@ def _gpu(name, okey, form):
     s = ev.spec
     return mf.Interpolant.from_overlaps(
         ev.nodes, standin.node_overlaps(ev), standin.standin_sigma(ev, ev.nodes), s.rank, s.eps,
-        s.modes, ev.det, s.t0, s.dt, s.d_ref, ev.metric, ev.centre, s.tail_degree, form, sky=ev.sky)
+        s.modes, ev.det, s.t0, s.dt, s.d_ref, ev.metric, ev.centre, s.tail_degree, form, sky=ev.sky,
+        kernel=s.kernel)
 
 
 def gpu_model(name, form="fp32", **over):

@@ -29,6 +29,7 @@ def test_paired_launch_bitwise_equal_to_single(cfg, Q, form):
         m.set_option("tc_pair", 1)
         b = _run(m, th, ex)
         assert m.sync_status()[0] == 0
+        assert m.query("tc_paired") == 1   # 3 passes: clusters of 6 CTAs are paired
     finally:
         m.set_option("tc_pair", 1)
         m.set_form("fp32")
@@ -37,3 +38,44 @@ def test_paired_launch_bitwise_equal_to_single(cfg, Q, form):
     if cfg == "C1":
         ref = _cases.oracle_model(cfg).loglike(th, ex)
         assert np.abs(b.astype(np.float64) - ref).max() <= 0.01
+
+
+def test_pairing_skipped_when_clusters_of_eight_idle_sms():
+    """4 passes would pair into clusters of 8 CTAs, which leave more SMs idle
+    than clusters of 4 on this GPU: the launch stays single (same results)."""
+    m = _cases.gpu_model("C2", N=1500, M=512)
+    th, ex = _cases.queries("C2", 700, seed=72, N=1500, M=512)
+    try:
+        m.set_form("bf16_3term")
+        assert m.query("n_pass") == 4
+        _run(m, th, ex)
+        assert m.query("tc_paired") == 0
+    finally:
+        m.set_form("fp32")
+
+
+def test_chunked_cluster_launches_equal_one_launch():
+    """A layout of 4 passes run as one cluster launch and as two launches of
+    2 passes each (option tc_chunk) gives bitwise the same lnL: every pass
+    partial is computed the same way, then summed in pass order."""
+    import torch
+    m = _cases.gpu_model("C2", N=1500, M=512)
+    th, ex = _cases.queries("C2", 1931, seed=71, N=1500, M=512)
+    d_th, d_ex = torch.from_numpy(th).cuda(), torch.from_numpy(ex).cuda()
+    try:
+        for form in ("bf16_3term", "fp16"):
+            m.set_form(form)
+            m.set_option("pass_count", 4)
+            assert m.query("n_pass") == 4
+            one = m.loglike(d_th, d_ex).cpu().numpy()
+            m.set_option("tc_chunk", 2)
+            two = m.loglike(d_th, d_ex).cpu().numpy()
+            cols1 = m.eval_columns(d_th[:300]).cpu().numpy()
+            m.set_option("tc_chunk", 0)
+            cols0 = m.eval_columns(d_th[:300]).cpu().numpy()
+            assert np.array_equal(one, two), form
+            assert np.array_equal(cols0, cols1), form
+    finally:
+        m.set_option("tc_chunk", 0)
+        m.set_option("pass_count", 0)
+        m.set_form("fp32")
