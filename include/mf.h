@@ -575,6 +575,12 @@ MF_API int mf_reweight(const double *logwt, const double *log_ratio, int n, doub
  *                resident CTAs of the single launch (mf_query "tc_paired"
  *                tells the last launch's choice); 0 = never.  Results are
  *                the same either way.
+ *   "tc_rot"   : 1 (default) = query tile t of the tcgen05 kernels visits the
+ *                node blocks starting at block 11 floor(t / 2) mod n_kb (the
+ *                clusters, which start together, then fetch different weight
+ *                tiles); 0 = every tile starts at block 0.  Changes the order
+ *                of the FP32 sums (results differ in rounding only); batched
+ *                launches take each member's setting.
  *   "tc_chunk" : passes per cluster launch at most (2..8); 0 (default) = as
  *                many as one CTA's shared memory stages (4 for the 3-term
  *                forms).  Columns needing more passes run as several

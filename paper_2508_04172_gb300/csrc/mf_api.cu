@@ -604,6 +604,11 @@ int mf_set_option(mf_handle *h, const char *key, double value) {
         h->tc_pair = (int)value;
         return MF_OK;
     }
+    if (k == "tc_rot") {   // rotate each query tile's node-block order (1, default) or not (0)
+        if (value != 0 && value != 1) return MF_E_INVAL;
+        h->tc_rot = (int)value;
+        return MF_OK;
+    }
     if (k == "tc_chunk") {   // passes per cluster launch at most (0: as many as fit)
         if (value < 0 || value > 8 || value != (int)value || value == 1) return MF_E_INVAL;
         h->tc_chunk = (int)value;

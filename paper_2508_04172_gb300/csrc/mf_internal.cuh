@@ -102,6 +102,7 @@ struct TcEvent {
     int nkb;                    // node blocks of 32 (Nk / 32)
     int nbox;                   // rows of one W tile = widest pass of this event
     int pair_ok;                // half-height maps exist (nbox / 2 a multiple of 8 rows)
+    int rot_mul;                // node-block order of tile t starts at rot_mul * (t / 2) mod n_kb (0: at 0)
 };
 
 // Per-call arguments of a batched launch (kernel parameter; < 32 KB).
@@ -189,6 +190,7 @@ struct mf_handle {
     int tc_pair = 1;                // 1: pair two query tiles per cluster when possible, 0: never
     int tc_chunk = 0;               // passes per cluster launch at most (0: as many as fit)
     int tc_paired = 0;              // the last cluster launch paired two query tiles
+    int tc_rot = 1;                 // 1: rotate each tile's node-block order (spreads weight reads), 0: no
     int nbox = 0;                   // rows (device columns) per W tile = widest pass
     // scratch
     unsigned long long *d_bad = nullptr;

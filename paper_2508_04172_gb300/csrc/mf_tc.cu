@@ -97,7 +97,9 @@ struct BatchSrc {
 // time.  Tiles 2i and 2i+1 share the order (the paired launch gives both the
 // same weight tiles); the order depends only on the tile, so a query's sum
 // is formed in the same order whatever the launch shape.
-__device__ __forceinline__ int tile_rot(int tile, int nkb) { return (int)(((long long)(tile >> 1) * 11) % nkb); }
+__device__ __forceinline__ int tile_rot(int tile, int nkb, int mul) {
+    return (int)(((long long)(tile >> 1) * mul) % nkb);
+}
 __device__ __forceinline__ int rot_kb(int kb, int rot, int nkb) {
     const int k = kb + rot;
     return k >= nkb ? k - nkb : k;
@@ -144,7 +146,7 @@ __device__ __forceinline__ void cursor_settle(NodeCursor &cu, const Src &src, in
         src.item(it, e, tile);
         const TcEvent &ev = src.event(e);
         cu.nkb = ev.nkb;
-        cu.rot = tile_rot(tile * pair + half, ev.nkb);
+        cu.rot = tile_rot(tile * pair + half, ev.nkb, ev.rot_mul);
         cu.nodes = ev.nodes_s;
         cu.kb = rank;
     }
@@ -269,7 +271,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                 const int col0 = ev.epi.passes[rank].col0;
                 const uint32_t bytes = (uint32_t)(NB * ev.nbox * kRowBytes);   // the whole tile lands here
                 const int nkb = ev.nkb;
-                const int rot = tile_rot(tile * PAIR + half, nkb);
+                const int rot = tile_rot(tile * PAIR + half, nkb, ev.rot_mul);
                 const int hrows = ev.nbox / 2;                                  // paired: rows this CTA loads
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(emptyB + s, ph ^ 1, err, 1, kb)) { ok = false; break; }
@@ -386,7 +388,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
             const EvIO io = src.io(e);
             const int N = ev.N, P = ev.P, nkb = ev.nkb;
             const int kind = ev.rot.rbf;
-            const int rot = tile_rot(tile, nkb);
+            const int rot = tile_rot(tile, nkb, ev.rot_mul);
             float2 X[RPT / 2][4];   // row pairs (rg + 2h RS, rg + (2h+1) RS), per coordinate
             float4 xu[RPT];
             {
@@ -821,6 +823,7 @@ int fill_tc_event(const mf_handle *h, TcEvent *ev) {
         memcpy(&ev->tm_lo2, h->tmap_lo2, sizeof(CUtensorMap));
     }
     ev->pair_ok = h->pair_ok ? 1 : 0;
+    ev->rot_mul = h->tc_rot ? 11 : 0;
     ev->epi = make_epi(h);
     ev->rot = make_rot(h);
     ev->nodes_s = h->d_nodes_s;

@@ -79,7 +79,9 @@ struct Tc2Call {
 // each pass's interpolated columns instead of combining them into lnL.
 // Node-block order of tile t: starts at 11 floor(t / 2) mod nkb and wraps
 // (the same order as the cluster design, so the two give bitwise equal sums).
-__device__ __forceinline__ int tile_rot2(int tile, int nkb) { return (int)(((long long)(tile >> 1) * 11) % nkb); }
+__device__ __forceinline__ int tile_rot2(int tile, int nkb, int mul) {
+    return (int)(((long long)(tile >> 1) * mul) % nkb);
+}
 
 template <int NM, int AT, int TERMS, bool COLS = false>
 __global__ void __launch_bounds__(kThreads2, 1)
@@ -139,7 +141,7 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
             bool ok = true;
             for (int it = blockIdx.x; it < c.n_items && ok; it += c.n_ctas) {
                 const int col0 = ev.epi.passes[it % c.n_pass].col0;
-                const int rot = tile_rot2(it / c.n_pass, nkb);
+                const int rot = tile_rot2(it / c.n_pass, nkb, ev.rot_mul);
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!mbar_wait(emptyB + s, ph ^ 1, err, 1, kb)) { ok = false; break; }
                     mbar_expect_tx(fullB + s, bytes);
@@ -213,7 +215,7 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
         float4 ynext = make_float4(0.f, 0.f, 0.f, 0.f);
         auto fetch = [&]() {
             if (nit < c.n_items && lane < 16) {
-                const int r = tile_rot2(nit / c.n_pass, nkb);
+                const int r = tile_rot2(nit / c.n_pass, nkb, ev.rot_mul);
                 const int kd = nkb_f + r < nkb ? nkb_f + r : nkb_f + r - nkb;
                 ynext = ldg_keep(ev.nodes_s + kd * kKB + 16 * h + lane);
             }
@@ -237,7 +239,7 @@ tc2_kernel(const __grid_constant__ TcEvent ev, const __grid_constant__ Tc2Call c
             const int kind = ev.rot.rbf;
             const float2 X0 = make_float2(x[0] * pre, x[0] * pre), X1 = make_float2(x[1] * pre, x[1] * pre);
             const float2 X2 = make_float2(x[2] * pre, x[2] * pre), X3 = make_float2(x[3] * pre, x[3] * pre);
-            const int rot = tile_rot2(tile, nkb);
+            const int rot = tile_rot2(tile, nkb, ev.rot_mul);
             for (int kb = 0; kb < nkb; ++kb) {
                 float4 *buf = scr + sbuf * 16;
                 sbuf ^= 1;
