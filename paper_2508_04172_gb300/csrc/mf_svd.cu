@@ -20,7 +20,7 @@
 //
 // The FP64 rate of this GPU is low, so every step that touches the N x M
 // matrix spreads over all SMs (tiled complex GEMM, split over k when the
-// output has few tiles); the Gram-Schmidt runs as three launches per column
+// output has few tiles); the Gram-Schmidt runs as six launches per column
 // with the cross-CTA sums done by the last CTA to finish (no waiting between
 // CTAs); only the b x b Jacobi runs in one CTA.
 //
