@@ -425,51 +425,60 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                 const int n0 = kd * kKB + c * 8;
                 float v[RPT][8];   // rows rg + RS j, nodes n0 .. n0+7
                 const bool full = (kd * kKB + kKB <= N);
+                if (full && kind == 0) {
+                    // the common case: 32 nodes, Gaussian kernel
 #pragma unroll
-                for (int e8 = 0; e8 < 8; ++e8) {
-                    const int n = n0 + e8;
-                    if (full || n < N) {
+                    for (int e8 = 0; e8 < 8; ++e8) {
                         const float4 y = scr[e8 * CPR + c];   // node c*8+e8 (conflict-free broadcast)
                         const float2 ny0 = make_float2(y.x, y.x), ny1 = make_float2(y.y, y.y);
                         const float2 ny2 = make_float2(y.z, y.z), ny3 = make_float2(y.w, y.w);
-                        if (kind == 0) {
+#pragma unroll
+                        for (int h2 = 0; h2 < RPT / 2; ++h2) {
+                            // r2 = |x - y|^2 - sc, so Phi * 2^sc = 2^-r2 (two rows at once)
+                            float2 dd = __fadd2_rn(X[h2][0], ny0);
+                            float2 r2 = __ffma2_rn(dd, dd, nsc);
+                            dd = __fadd2_rn(X[h2][1], ny1);
+                            r2 = __ffma2_rn(dd, dd, r2);
+                            dd = __fadd2_rn(X[h2][2], ny2);
+                            r2 = __ffma2_rn(dd, dd, r2);
+                            dd = __fadd2_rn(X[h2][3], ny3);
+                            r2 = __ffma2_rn(dd, dd, r2);
+                            v[2 * h2][e8] = ex2(-r2.x);
+                            v[2 * h2 + 1][e8] = ex2(-r2.y);
+                        }
+                    }
+                } else {
+                    // the last node block (tail monomials, padding) or another kernel
+#pragma unroll
+                    for (int e8 = 0; e8 < 8; ++e8) {
+                        const int n = n0 + e8;
+                        if (full || n < N) {
+                            const float4 y = scr[e8 * CPR + c];
+                            const float2 ny0 = make_float2(y.x, y.x), ny1 = make_float2(y.y, y.y);
+                            const float2 ny2 = make_float2(y.z, y.z), ny3 = make_float2(y.w, y.w);
 #pragma unroll
                             for (int h2 = 0; h2 < RPT / 2; ++h2) {
-                                // r2 = |x - y|^2 - sc, so Phi * 2^sc = 2^-r2 (two rows at once)
+                                // Gaussian: r2 = |x - y|^2 - sc as above; other kernels:
+                                // phi(s^2) with s^2 = |pre (x - y)|^2, times 2^sc
                                 float2 dd = __fadd2_rn(X[h2][0], ny0);
-                                float2 r2 = __ffma2_rn(dd, dd, nsc);
+                                float2 r2 = __ffma2_rn(dd, dd, kind == 0 ? nsc : make_float2(0.f, 0.f));
                                 dd = __fadd2_rn(X[h2][1], ny1);
                                 r2 = __ffma2_rn(dd, dd, r2);
                                 dd = __fadd2_rn(X[h2][2], ny2);
                                 r2 = __ffma2_rn(dd, dd, r2);
                                 dd = __fadd2_rn(X[h2][3], ny3);
                                 r2 = __ffma2_rn(dd, dd, r2);
-                                v[2 * h2][e8] = ex2(-r2.x);
-                                v[2 * h2 + 1][e8] = ex2(-r2.y);
+                                v[2 * h2][e8] = kind == 0 ? ex2(-r2.x) : rbf_other(kind, r2.x) * tsc;
+                                v[2 * h2 + 1][e8] = kind == 0 ? ex2(-r2.y) : rbf_other(kind, r2.y) * tsc;
                             }
                         } else {
+                            // tail monomials 1, x1..x4 (times 2^sc), then zero padding
+                            const int q = n - N;
 #pragma unroll
-                            for (int h2 = 0; h2 < RPT / 2; ++h2) {
-                                // the other radial kernels: phi(s^2), s^2 = |pre (x - y)|^2
-                                float2 dd = __fadd2_rn(X[h2][0], ny0);
-                                float2 r2 = __fmul2_rn(dd, dd);
-                                dd = __fadd2_rn(X[h2][1], ny1);
-                                r2 = __ffma2_rn(dd, dd, r2);
-                                dd = __fadd2_rn(X[h2][2], ny2);
-                                r2 = __ffma2_rn(dd, dd, r2);
-                                dd = __fadd2_rn(X[h2][3], ny3);
-                                r2 = __ffma2_rn(dd, dd, r2);
-                                v[2 * h2][e8] = rbf_other(kind, r2.x) * tsc;
-                                v[2 * h2 + 1][e8] = rbf_other(kind, r2.y) * tsc;
+                            for (int j = 0; j < RPT; ++j) {
+                                float m = (q == 0) ? 1.f : (q == 1) ? xu[j].x : (q == 2) ? xu[j].y : (q == 3) ? xu[j].z : xu[j].w;
+                                v[j][e8] = (q < P) ? m * tsc : 0.f;
                             }
-                        }
-                    } else {
-                        // tail monomials 1, x1..x4 (times 2^sc), then zero padding
-                        const int q = n - N;
-#pragma unroll
-                        for (int j = 0; j < RPT; ++j) {
-                            float m = (q == 0) ? 1.f : (q == 1) ? xu[j].x : (q == 2) ? xu[j].y : (q == 3) ? xu[j].z : xu[j].w;
-                            v[j][e8] = (q < P) ? m * tsc : 0.f;
                         }
                     }
                 }
