@@ -215,7 +215,10 @@ MF_API int mf_set_rotation(mf_handle *h, const double *metric, const double *cen
 MF_API int mf_set_frame(mf_handle *h, const double *A, const double *centre);
 
 /* Select the Phi.W arithmetic (default MF_FORM_FP32).  Converts the weights
- * for the form on first use (synchronous on the legacy stream). */
+ * for the form on first use (synchronous on the legacy stream).  Returns
+ * MF_E_NOTIMPL for an FP16 form on a handle built with MF_RBF_PHS3 or
+ * MF_RBF_MQ (their values leave the FP16 range), MF_E_STATE for MF_FORM_MLP
+ * before mf_train_surrogate; the previous form stays selected then. */
 MF_API int mf_set_form(mf_handle *h, mf_form form);
 
 /*
