@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 namespace mf {
 namespace {
@@ -193,6 +194,12 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                                         const int nc, const int E, unsigned *err, float *cols = nullptr,
                                         const int *umap = nullptr, int K = 0) {
     constexpr int NA = (TERMS == 3) ? 2 : 1;
+    // How an RBF tile reaches the other CTAs of the cluster: each producer warp
+    // copies its own rows as soon as it has written them (single-event, unpaired
+    // launches: measured 9 % faster on C2), or the eight producer warps meet at a
+    // barrier and one thread copies the whole tile (paired launches, where the
+    // many small copies slowed C1 / C4 by 15-19 %, and the batched kernel)
+    constexpr bool kWarpCopies = PAIR == 1 && std::is_same<Src, SingleSrc>::value;
     constexpr int NB = (TERMS >= 2) ? 2 : 1;
     constexpr int SP = kSlotsPerProducer;
     // FP16 forms carry Phi * 2^14 (W columns are scaled to match)
@@ -224,7 +231,9 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < nslot; ++i) {
-            mbar_init(fullA + i, 1);
+            // own slots: one arrival per producer warp; other CTAs' slots: the
+            // arming arrival, completed by their copies' transaction bytes
+            mbar_init(fullA + i, kWarpCopies && i / SP == rank ? (uint32_t)kProdWarps : 1u);
             mbar_init(emptyA + i, (uint32_t)np);
         }
         for (int i = 0; i < SB; ++i) {
@@ -355,6 +364,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
         constexpr int CPR = kKB / 8;                // 16-byte chunks per row
         constexpr int RS = 256 / CPR;               // row stride between a thread's rows
         constexpr int RPT = kTile / RS;             // rows per thread (2 or 4)
+        static_assert(CPR == 4, "a producer warp's rows must be whole 8-row swizzle atoms");
         const int pt = threadIdx.x - 64;            // 0..255
         const int c = pt % CPR, rg = pt / CPR;      // chunk (8 nodes); rows rg + RS j
         const float2 nsc = make_float2(-kPhiLog2, -kPhiLog2);
@@ -513,15 +523,42 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                     }
                     fence_async_smem();
                 }
-                // all producer warps wrote the slot; and all agree whether to go on
-                if (!bar_and_256(got)) { ok = false; break; }
-                if (pt == 0) {
-                    // local slot: plain arrive; other CTAs: bulk copy completing
-                    // as transaction bytes on their (pre-armed) fullA barrier
-                    const uint32_t src_a = su32(base), fa = su32(fullA + sa);
-                    for (int dst = 0; dst < np; ++dst)
-                        if (dst != rank)
-                            bulk_copy_to_cta(map_cta(src_a, hbase + dst), src_a, abytes, map_cta(fa, hbase + dst));
+                if (!kWarpCopies) {
+                    // all producer warps wrote the slot; and all agree whether to go on
+                    if (!bar_and_256(got)) { ok = false; break; }
+                    if (pt == 0) {
+                        // local slot: plain arrive; other CTAs: bulk copy completing
+                        // as transaction bytes on their (pre-armed) fullA barrier
+                        const uint32_t src_a = su32(base), fa = su32(fullA + sa);
+                        for (int dst = 0; dst < np; ++dst)
+                            if (dst != rank)
+                                bulk_copy_to_cta(map_cta(src_a, hbase + dst), src_a, abytes,
+                                                 map_cta(fa, hbase + dst));
+                        mbar_arrive(fullA + sa);
+                    }
+                    ++u;
+                    continue;
+                }
+                if (!got) { ok = false; break; }   // warp-uniform (broadcast above)
+                __syncwarp();
+                if (lane == 0) {
+                    // this warp's rows are whole 8-row swizzle atoms (rows
+                    // 8 w' .. 8 w' + 7 + RS j); each goes to the other CTAs by a
+                    // bulk copy completing as transaction bytes on their
+                    // (pre-armed) fullA barrier, and this warp arrives on its own
+                    const uint32_t fa = su32(fullA + sa);
+                    const int wp = warp - 2;
+#pragma unroll
+                    for (int j = 0; j < RPT; ++j)
+#pragma unroll
+                        for (int part = 0; part < NA; ++part) {
+                            const uint32_t src =
+                                su32(base) + (uint32_t)(part * kATile + (wp + (RS >> 3) * j) * 8 * kRowBytes);
+                            for (int dst = 0; dst < np; ++dst)
+                                if (dst != rank)
+                                    bulk_copy_to_cta(map_cta(src, hbase + dst), src, 8 * kRowBytes,
+                                                     map_cta(fa, hbase + dst));
+                        }
                     mbar_arrive(fullA + sa);
                 }
                 ++u;
