@@ -196,10 +196,12 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
     constexpr int NA = (TERMS == 3) ? 2 : 1;
     // How an RBF tile reaches the other CTAs of the cluster: each producer warp
     // copies its own rows as soon as it has written them (single-event, unpaired
-    // launches: measured 9 % faster on C2), or the eight producer warps meet at a
-    // barrier and one thread copies the whole tile (paired launches, where the
-    // many small copies slowed C1 / C4 by 15-19 %, and the batched kernel)
-    constexpr bool kWarpCopies = PAIR == 1 && std::is_same<Src, SingleSrc>::value;
+    // launches of 4 or more passes: measured 9 % faster on C2), or the eight
+    // producer warps meet at a barrier and one thread copies the whole tile
+    // (paired launches, where the many small copies slowed C1 / C4 by 15-19 %;
+    // 3-pass unpaired launches, 5-8 % slower with them; the batched kernel)
+    constexpr bool kWarpCopiesAllowed = PAIR == 1 && std::is_same<Src, SingleSrc>::value;
+    const bool warp_copies = kWarpCopiesAllowed && np >= 4;
     constexpr int NB = (TERMS >= 2) ? 2 : 1;
     constexpr int SP = kSlotsPerProducer;
     // FP16 forms carry Phi * 2^14 (W columns are scaled to match)
@@ -233,7 +235,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
         for (int i = 0; i < nslot; ++i) {
             // own slots: one arrival per producer warp; other CTAs' slots: the
             // arming arrival, completed by their copies' transaction bytes
-            mbar_init(fullA + i, kWarpCopies && i / SP == rank ? (uint32_t)kProdWarps : 1u);
+            mbar_init(fullA + i, warp_copies && i / SP == rank ? (uint32_t)kProdWarps : 1u);
             mbar_init(emptyA + i, (uint32_t)np);
         }
         for (int i = 0; i < SB; ++i) {
@@ -523,7 +525,7 @@ __device__ __forceinline__ void tc_body(const Src &src, const int np, const int 
                     }
                     fence_async_smem();
                 }
-                if (!kWarpCopies) {
+                if (!warp_copies) {
                     // all producer warps wrote the slot; and all agree whether to go on
                     if (!bar_and_256(got)) { ok = false; break; }
                     if (pt == 0) {
