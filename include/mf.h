@@ -151,6 +151,23 @@ MF_API int mf_build(const double *nodes, const double *node_values, int N, int K
 MF_API int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m, int rank);
 
 /*
+ * Host-only planner: the device column layout a handle with this layout
+ * would take for a form whose passes are at most pass_max columns wide
+ * (16..512, a multiple of 16; 176 for MF_FORM_FP32, 256 for the tcgen05
+ * cluster design) and, with pass_count > 0, exactly that many passes.
+ * Per detector its mode groups (interleaved Re/Im of a run of SVD
+ * coefficients, padded to 8 columns) then its cross-term group, packed
+ * contiguously into the fewest passes that fit, the widest pass minimised;
+ * a mode's coefficients are split into runs when whole modes do not fit.
+ *   n_pass, pass_width [<= 48], Kdev: out, the passes and their padded total.
+ *   user_of_dev: out or NULL, [Kdev] node_values column of each device
+ *                column (-1 for padding); cap = its length.
+ * Touches no GPU.  MF_E_INVAL if nothing fits or an argument is out of range.
+ */
+MF_API int mf_plan_layout(int n_det, int n_modes, int rank, int pass_max, int pass_count, int *n_pass,
+                          int *pass_width, int *Kdev, int *user_of_dev, int cap);
+
+/*
  * SVD basis vectors of every (detector, mode) overlap series (Eq. SVD).
  *   basis : host [n_det][n_modes][rank][M][2] FP64 (re, im).
  *   t0, dt: time of sample 0 and the sample spacing (seconds).

@@ -16,7 +16,7 @@ from .build import SO as _SO_PATH, build
 
 __all__ = ["build", "lib", "MFError", "Interpolant", "Batch", "loglike_batch", "Mlp",
            "svd_compress", "FORMS", "pack_node_values", "nested_sample", "reweight", "Wave", "place_nodes",
-           "squeeze_factor", "standin_overlaps"]
+           "squeeze_factor", "standin_overlaps", "plan_layout"]
 
 MF_OK, MF_E_INVAL, MF_E_NOMEM, MF_E_CUDA = 0, -1, -2, -3
 MF_E_ILLCOND, MF_E_RANGE, MF_E_TIMEOUT, MF_E_NOTIMPL, MF_E_STATE = -4, -5, -6, -7, -8
@@ -144,6 +144,7 @@ def lib():
         L.mf_nested_sample.argtypes = [vp, ctypes.POINTER(NsParams), ctypes.POINTER(NsResult), vp, vp, vp,
                                        ip, vp]
         L.mf_reweight.argtypes = [vp, vp, ip, vp, ctypes.POINTER(dp)]
+        L.mf_plan_layout.argtypes = [ip, ip, ip, ip, ip, ctypes.POINTER(ip), vp, ctypes.POINTER(ip), vp, ip]
         _lib = L
     return _lib
 
@@ -177,6 +178,20 @@ def svd_compress(Z: np.ndarray, rank: int, stream=None):
                                  _stream_ptr(stream) if stream is not None else None),
            "mf_svd_compress")
     return coef, basis, sv
+
+
+def plan_layout(n_det, n_modes, rank, pass_max, pass_count=0):
+    """mf_plan_layout (host only): (pass widths [n_pass], user column of each
+    device column [Kdev], -1 for padding)."""
+    n_pass = ctypes.c_int()
+    kdev = ctypes.c_int()
+    widths = np.zeros(48, np.int32)
+    _check(lib().mf_plan_layout(n_det, n_modes, rank, pass_max, pass_count, ctypes.byref(n_pass), _ptr(widths),
+                                ctypes.byref(kdev), None, 0), "mf_plan_layout")
+    u = np.empty(kdev.value, np.int32)
+    _check(lib().mf_plan_layout(n_det, n_modes, rank, pass_max, pass_count, ctypes.byref(n_pass), _ptr(widths),
+                                ctypes.byref(kdev), _ptr(u), kdev.value), "mf_plan_layout")
+    return widths[:n_pass.value].copy(), u
 
 
 def place_nodes(metric, centre, mismatch, squeeze, N, skip=0):

@@ -412,6 +412,30 @@ int mf_set_layout(mf_handle *h, int n_det, int n_modes, const int *ell_m, int ra
     return mf::prepare_form(h, h->form);
 }
 
+int mf_plan_layout(int n_det, int n_modes, int rank, int pass_max, int pass_count, int *n_pass, int *pass_width,
+                   int *Kdev, int *user_of_dev, int cap) {
+    if (!n_pass || !pass_width || !Kdev || n_det < 1 || n_det > mf::kMaxDet || n_modes < 1 ||
+        n_modes > mf::kMaxModes || rank < 1 || rank > 128 || pass_max < 16 || pass_max > 512 || pass_max % 16 ||
+        pass_count < 0 || pass_count > mf::kMaxPass || cap < 0)
+        return MF_E_INVAL;
+    mf_handle h;   // host fields only: no device memory is touched
+    h.n_det = n_det;
+    h.n_modes = n_modes;
+    h.rank = rank;
+    h.pass_max = pass_max;
+    h.pass_count = pass_count;
+    const int rc = mf::build_layout(&h);
+    if (rc) return rc;
+    *n_pass = (int)h.passes.size();
+    for (int p = 0; p < *n_pass; ++p) pass_width[p] = h.passes[p].width;
+    *Kdev = h.Kdev;
+    if (user_of_dev) {
+        if (cap < h.Kdev) return MF_E_INVAL;
+        for (int c = 0; c < h.Kdev; ++c) user_of_dev[c] = h.user_of_dev[c];
+    }
+    return MF_OK;
+}
+
 int mf_set_basis(mf_handle *h, const double *basis, int M, double t0, double dt) {
     if (!h || !basis || M < mf::kStencil || !(dt > 0)) return MF_E_INVAL;
     if (!h->have_layout) return MF_E_STATE;
