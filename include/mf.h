@@ -421,8 +421,8 @@ MF_API int mf_mlp_query(const mf_mlp *m, const char *key, double *value);
  * maps the metric-eigenbasis point x = R (theta - centre) to the per-column
  * standardised interpolated columns (node_values order); it is trained on
  * the GPU (mf_mlp kernels) on n_train points labelled by the FP64 RBF
- * interpolant, itself evaluated on the GPU (FP64 kernel sums and a cuBLAS
- * DGEMM against the FP64 weights).
+ * interpolant, itself evaluated on the GPU (FP64 kernel sums and the
+ * library's own FP64 GEMM against the FP64 weights).
  *   train_intrinsic : device [n_train][4] FP32 sampler-frame points (16-byte
  *                     aligned), drawn from the region the sampler explores.
  *   held_*          : device held-out queries [n_held][4], [n_held][E].
@@ -587,8 +587,10 @@ MF_API int mf_reweight(const double *logwt, const double *log_ratio, int n, doub
  *                -1 (default) = 1 when the columns fit in one such pass,
  *                else 0.  Re-lays out the weights; mf_query "tc_design"
  *                reports the design in use.
- *   "tc_nbs"   : depth (2..4) of the weight-tile ring of the tcgen05 kernel;
- *                0 (default) = deepest that fits in shared memory.
+ *   "tc_nbs"   : depth (2..6) of the weight-tile ring of the tcgen05
+ *                kernels, lowered to what fits in shared memory; 0 (default)
+ *                = 4 for the cluster design, 6 for the tensor-memory design
+ *                (likewise lowered).
  *   "tc_pair"  : 1 (default) = the 3-term forms pair two query tiles per
  *                cluster when 2 x passes <= 8 (weight tiles multicast to
  *                both) and the larger clusters keep at least 93 % of the
