@@ -96,10 +96,11 @@ static int split_exact(const std::vector<int> &w, int count, std::vector<int> &s
 // of a run of SVD coefficients, padded to 8 columns) then its cross-term
 // group, packed contiguously into passes of at most pass_max columns (each
 // padded to 16).  The layout takes the fewest passes that fit (or exactly
-// pass_count), balanced by a min-max split; when a mode's coefficients do
-// not pack into that many passes as whole groups, every mode is split into
+// pass_count), balanced by a min-max split.  Every mode may be split into
 // 2, 4, ... runs of coefficients (lnL is linear in each coefficient, so a
-// mode's contribution may be summed over passes).
+// mode's contribution may be summed over passes): needed when whole modes
+// do not pack into that many passes, and taken when a finer split makes the
+// widest pass narrower.
 int build_layout(mf_handle *h) {
     const int nd = h->n_det, nm = h->n_modes, l = h->rank;
     auto up = [](int x, int a) { return (x + a - 1) / a * a; };
@@ -121,20 +122,26 @@ int build_layout(mf_handle *h) {
     std::vector<G> gs;
     std::vector<int> cut_at;
     bool found = false;
+    // fewest passes first; among the splits of the modes that fit that many,
+    // the one whose widest pass is narrowest (a cluster advances at the pace
+    // of its widest pass), the coarsest on ties
     for (int npass = 1; npass <= kMaxPass && !found; ++npass) {
         if (h->pass_count > 0 && npass != h->pass_count) continue;
-        for (int nsplit = 1; nsplit <= 32 && !found; nsplit *= 2) {
+        int best = pmax + 1;
+        for (int nsplit = 1; nsplit <= 32; nsplit *= 2) {
             std::vector<G> cand = make(nsplit);
             if ((int)cand.size() > kMaxGroups) break;
             int total = 0, gmax = 0;
             for (auto &g : cand) { total += g.width; gmax = std::max(gmax, g.width); }
             if (up(gmax, kPassAlign) > pmax) continue;       // a finer split may fit
-            if (npass * pmax < total || npass > (int)cand.size()) break;
+            if (npass * pmax < total) break;                   // finer splits only add padding
+            if (npass > (int)cand.size()) continue;            // a finer split has more groups
             std::vector<int> w;
             for (auto &g : cand) w.push_back(g.width);
             std::vector<int> start;
             const int widest = split_exact(w, npass, start);
-            if (widest > 0 && widest <= pmax) {
+            if (widest > 0 && widest < best) {
+                best = widest;
                 gs = cand;
                 cut_at = start;
                 found = true;

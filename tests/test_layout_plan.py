@@ -3,8 +3,9 @@ the lnL kernels run on.  The interpolated columns of Eq. rbfcoeff (per
 detector and mode the real then imaginary parts of the SVD coefficients of
 Eq. SVD, then the cross terms) are regrouped into passes; these tests check
 that the plan is a permutation of the user columns plus padding, keeps each
-coefficient's Re/Im pair adjacent, respects the pass width and takes the
-fewest passes.  No GPU is touched."""
+coefficient's Re/Im pair adjacent, respects the pass width, takes the
+fewest passes and, among plans of that many passes, one whose widest pass is
+narrowest.  No GPU is touched."""
 import ctypes
 
 import numpy as np
@@ -82,13 +83,26 @@ def test_plan_takes_the_fewest_passes(nd, nm, rank, pmax):
 def test_workload_pass_counts():
     """The pass counts the kernels are tuned for: rank 20 / 3 detectors in 3
     passes, rank 40 / 3 detectors in 4, rank 80 / 1 detector in 3 (each mode
-    split into two runs of 40 coefficients: whole modes of 160 columns do not
-    pack into 3 passes of 256), 4 band channels of rank 40 in 6."""
-    assert len(mf.plan_layout(3, 4, 20, 256)[0]) == 3
+    split into runs of 12 coefficients: whole modes of 160 columns do not
+    pack into 3 passes of 256, and runs of 40 would leave passes of
+    240 / 240 / 176), 4 band channels of rank 40 in 6 of at most 240."""
+    assert list(mf.plan_layout(3, 4, 20, 256)[0]) == [176, 176, 176]
     assert len(mf.plan_layout(3, 4, 40, 256)[0]) == 4
     w, u = mf.plan_layout(1, 4, 80, 256)
-    assert list(w) == [240, 240, 176]
-    assert len(mf.plan_layout(4, 4, 40, 256)[0]) == 6
+    assert list(w) == [208, 224, 224]
+    w, _ = mf.plan_layout(4, 4, 40, 256)
+    assert len(w) == 6 and max(w) == 240
+
+
+@pytest.mark.parametrize("nd,nm,rank,pmax", CASES)
+def test_widest_pass_is_the_narrowest_possible(nd, nm, rank, pmax):
+    """With the pass count fixed, no plan has a narrower widest pass: asking
+    for the same count with pass_max one alignment step below it fails."""
+    widths, _ = mf.plan_layout(nd, nm, rank, pmax)
+    n, widest = len(widths), int(widths.max())
+    if widest > 16:
+        with pytest.raises(mf.MFError):
+            mf.plan_layout(nd, nm, rank, widest - 16, pass_count=n)
 
 
 @pytest.mark.parametrize("count", [2, 4, 5, 8])
