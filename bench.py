@@ -359,6 +359,8 @@ def run_ours(args):
             tag, srcs = "tc_kernel", ["paper_2508_04172_gb300/csrc/mf_tc.cu",
                                       "paper_2508_04172_gb300/csrc/mf_epilogue.cuh",
                                       "paper_2508_04172_gb300/csrc/mf_ptx.cuh"]
+        # the column layout (passes, weight tiles) is planned in the API source
+        srcs.append("paper_2508_04172_gb300/csrc/mf_api.cu")
     achieved = flops / (kms / 1e3) / 1e12
     roof.update(achieved=round(achieved, 2), frac=round(achieved / roof["peak"], 4),
                 traffic=_traffic_from_profile(f"{tag}@{spec.name}", srcs), kernel=tag,
@@ -630,7 +632,7 @@ def run_batch(args):
             "achieved": round(achieved, 2), "frac": round(achieved / bf16, 4),
             "traffic": _traffic_from_profile("tc_batch_kernel@C3", [
                 "paper_2508_04172_gb300/csrc/mf_tc.cu", "paper_2508_04172_gb300/csrc/mf_epilogue.cuh",
-                "paper_2508_04172_gb300/csrc/mf_ptx.cuh"]),
+                "paper_2508_04172_gb300/csrc/mf_ptx.cuh", "paper_2508_04172_gb300/csrc/mf_api.cu"]),
             "kernel": "tc_batch_kernel", "algorithmic_flops_per_launch": flops,
             "kernel_ms": round(kms, 4)}
 
