@@ -85,3 +85,31 @@ def test_batch_network_and_surrogate_entry_points_reject_bad_arguments():
     # the no-allocation path and the column evaluation reject NULL handles too
     assert L.mf_loglike_noalloc(None, None, None, 16, 5, None, None) == mf.MF_E_INVAL
     assert L.mf_eval_columns(None, None, 16, None, None) == mf.MF_E_INVAL
+
+
+def test_no_cpu_fallback_without_a_device():
+    """With valid arguments but no CUDA device, the library fails with
+    MF_E_CUDA instead of computing anything on the host, and the binding
+    turns that into an exception."""
+    import numpy as np
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    L = mf.lib()
+    rng = np.random.default_rng(0)
+    nodes = rng.uniform(-0.5, 0.5, (40, 4))
+    vals = rng.standard_normal((40, 3))
+    h = ctypes.c_void_p()
+    rc = L.mf_build(nodes.ctypes.data, vals.ctypes.data, 40, 3, mf.RBF_KERNELS.index("gaussian"), 1.5, 1, None,
+                    ctypes.byref(h))
+    assert rc == mf.MF_E_CUDA and not h.value
+    with pytest.raises(mf.MFError):
+        mf.Interpolant(nodes, vals, 1.5, 1)
+
+
+def test_binding_raises_when_the_library_is_missing(monkeypatch, tmp_path):
+    """No silent fallback in the binding either: without libmf.so it raises."""
+    monkeypatch.setattr(mf, "_lib", None)
+    monkeypatch.setattr(mf, "_SO_PATH", str(tmp_path / "libmf.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        mf.lib()
