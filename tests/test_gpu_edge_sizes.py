@@ -134,3 +134,42 @@ def test_batches_beyond_the_largest_are_refused():
                                 st) == mf.MF_E_INVAL
     torch.cuda.synchronize()
     assert torch.all(out == 0)
+
+
+def test_batch_member_with_fewer_node_blocks_than_passes():
+    """One persistent launch over a 2-block interpolant (N = 40, 3 passes) and
+    the full C1 interpolant, with batches of 1, 129 and 2000 queries: each
+    event equals its own single launch bit for bit, and the oracle within the
+    bound."""
+    import torch
+    import paper_2508_04172_gb300 as mf
+    over = dict(N=40, eps=2.0)
+    tiny, om_tiny = _from_oracle("C1", **over)
+    big, om_big = _cases.gpu_model("C1"), _cases.oracle_model("C1")
+    members = [(tiny, om_tiny, over, 1), (big, om_big, {}, 129), (tiny, om_tiny, over, 2000),
+               (big, om_big, {}, 1)]
+    hq = [_cases.queries("C1", q, seed=90 + i, **o) for i, (_, _, o, q) in enumerate(members)]
+    dth = [torch.from_numpy(th).cuda() for th, _ in hq]
+    dex = [torch.from_numpy(ex).cuda() for _, ex in hq]
+    b = None
+    try:
+        for m in (tiny, big):
+            m.set_form("bf16_3term")
+        b = mf.Batch([m for m, _, _, _ in members], [q for _, _, _, q in members], autotune=False)
+        outs = b.loglike(dth, dex)
+        torch.cuda.synchronize()
+        assert b.sync_status()[0] == 0
+        assert int(b.query("n_pass")) == 3
+        got = [o.cpu().numpy() for o in outs]
+        single = []
+        for (m, _, _, _), t, e in zip(members, dth, dex):
+            single.append(m.loglike(t, e).cpu().numpy())
+    finally:
+        if b is not None:
+            b.close()                     # before its members
+        big.set_form("fp32")
+        tiny.close()
+    for (m, om, _, q), (th, ex), g, s in zip(members, hq, got, single):
+        assert g.shape == (q,) and np.all(np.isfinite(g))
+        assert np.array_equal(g, s)
+        assert np.abs(g.astype(np.float64) - om.loglike(th, ex)).max() <= TOL
