@@ -173,3 +173,30 @@ def test_batch_member_with_fewer_node_blocks_than_passes():
         assert g.shape == (q,) and np.all(np.isfinite(g))
         assert np.array_equal(g, s)
         assert np.abs(g.astype(np.float64) - om.loglike(th, ex)).max() <= TOL
+
+
+@pytest.mark.parametrize("cfg", ["C1", "C1S"])
+@pytest.mark.parametrize("form", ["fp32", "bf16_3term"])
+def test_extreme_extrinsics(cfg, form):
+    """The ends of every extrinsic range: face-on and face-away (cos iota =
+    +-1, one helicity only), psi = 0 and pi, phi_c = 0 and 2 pi, d_L at both
+    ends of the prior, and with sky-dependent patterns a source at either
+    celestial pole and alpha = 0 and 2 pi: the oracle within the bound."""
+    th, ex = _cases.queries(cfg, 840, seed=95)
+    ex = ex.copy()
+    ex[0::4, 1], ex[1::4, 1] = 1.0, -1.0
+    ex[0::3, 2], ex[1::3, 2] = 0.0, np.float32(np.pi)
+    ex[0::5, 3], ex[1::5, 3] = 0.0, np.float32(2 * np.pi)
+    ex[0::7, 0], ex[1::7, 0] = 100.0, 400.0
+    if ex.shape[1] >= 7:
+        ex[0::6, 6], ex[1::6, 6] = np.float32(np.pi / 2), np.float32(-np.pi / 2)
+        ex[0::8, 5], ex[1::8, 5] = 0.0, np.float32(2 * np.pi)
+    m = _cases.gpu_model(cfg)
+    m.sync_status()
+    try:
+        m.set_form(form)
+        got = _run(m, th, ex)
+    finally:
+        m.set_form("fp32")
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - _cases.oracle_model(cfg).loglike(th, ex)).max() <= TOL
