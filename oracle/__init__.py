@@ -30,20 +30,27 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "libmforacle.so")
 _lock = threading.Lock()
+# how mforacle.c is compiled: OpenMP over queries, strict IEEE FP64 arithmetic
+GCC_FLAGS = ["-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99", "-D_DEFAULT_SOURCE",
+             "-fno-fast-math", "-ffp-contract=off"]
 _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile mforacle.c with gcc (-O2, OpenMP, strict IEEE: no fast-math)."""
+    """Compile mforacle.c with gcc (-O2, OpenMP, strict IEEE: no fast-math).
+    With MFORACLE_SO set, that already-built library is used instead: the
+    oracle's mutation test points it at copies of mforacle.c with a planted
+    mistake, to show that the pins catch each one."""
+    override = os.environ.get("MFORACLE_SO")
+    if override:
+        return override
     src = os.path.join(_HERE, "mforacle.c")
     if (not force and os.path.exists(_SO)
             and os.path.getmtime(_SO) >= os.path.getmtime(src)):
         return _SO
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _SO + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c99",
-                           "-D_DEFAULT_SOURCE", "-fno-fast-math", "-ffp-contract=off",
-                           src, "-o", tmp, "-lm"])
+    subprocess.check_call(["gcc", *GCC_FLAGS, src, "-o", tmp, "-lm"])
     os.replace(tmp, _SO)
     return _SO
 
