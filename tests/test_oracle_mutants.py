@@ -12,10 +12,18 @@ cross terms (Eq. conjugation_symmetry), the 2 psi rotation of the antenna
 patterns, the spline's not-a-knot ends and stencil (Sec. II D), the tail
 monomials and kernel of Eq. (rbfcoeff), the Delta-e rotation, the
 Wigner-d sum of Eq. (h_spherical_harmonic_basis), and the sky response's
-delay, wave-frame axes and hour angle (Eq. projected_h_td)."""
+delay, wave-frame axes and hour angle (Eq. projected_h_td).
+
+The NumPy parts of the oracle get the same treatment: a copy of the oracle
+package with one planted mistake is imported ahead of the real one in a
+child process that runs the pin suites of that module (the start-up solve
+and SVD, the metric rotation and column packing, the start-up generation
+of Sec. II C, the nested sampler and the network); the unmutated copy runs
+them all."""
 import concurrent.futures as cf
 import os
 import re
+import shutil
 import subprocess
 import sys
 
@@ -26,6 +34,14 @@ import oracle
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "mforacle.c")
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_sky.py", "tests/test_oracle_rbf_kernels.py"]
+ALL_PIN_FILES = PIN_FILES + ["tests/test_oracle_startup.py", "tests/test_oracle_nested.py",
+                             "tests/test_oracle_mlp.py"]
+# the pin suites that exercise each module of the oracle package
+PINS_OF = {"__init__.py": ["tests/test_oracle_pins.py", "tests/test_oracle_rbf_kernels.py",
+                           "tests/test_oracle_startup.py"],
+           "startup.py": ["tests/test_oracle_startup.py"],
+           "nested.py": ["tests/test_oracle_nested.py"],
+           "mlp.py": ["tests/test_oracle_mlp.py"]}
 
 # name -> (text in mforacle.c, replacement); each text occurs exactly once
 MUTANTS = {
@@ -99,6 +115,112 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
         dirs[name].mkdir()
     with cf.ThreadPoolExecutor(max_workers=max(1, min(6, (os.cpu_count() or 2) // 2))) as ex:
         futs = {name: ex.submit(_build_and_run, name, text, str(dirs[name])) for name, text in jobs.items()}
+        res = {name: f.result() for name, f in futs.items()}
+    rc, info = res.pop("(unmutated)")
+    assert rc == 0, f"the unmutated oracle fails its pins under the harness: {info}"
+    missed = {name: info for name, (rc, info) in res.items() if rc != 1}
+    assert not missed, f"planted mistakes that no pin caught: {missed}"
+
+
+# name -> (file of the oracle package, text, replacement); each text occurs once
+PY_MUTANTS = {
+    "SVD coefficients without the conjugate of V":
+        ("__init__.py", "C = Z @ B.conj().T", "C = Z @ B.T"),
+    "side condition P^T a = 0 dropped":
+        ("__init__.py", "A[N:, :N] = Pm.T", "A[N:, N:] = np.eye(P)"),
+    "tail with squared coordinates":
+        ("__init__.py", "Pm = np.concatenate([np.ones((N, 1)), nodes], axis=1)[:, :P]",
+         "Pm = np.concatenate([np.ones((N, 1)), nodes ** 2], axis=1)[:, :P]"),
+    "metric eigenvectors as columns":
+        ("__init__.py", "R = V[:, np.argsort(w)].T.copy()", "R = V[:, np.argsort(w)].copy()"),
+    "metric eigenvectors by descending eigenvalue":
+        ("__init__.py", "R = V[:, np.argsort(w)].T.copy()", "R = V[:, np.argsort(-w)].T.copy()"),
+    "Re and Im of the cross terms swapped in the packing":
+        ("__init__.py", "cols.append(sigma[k][:, iu[0], iu[1]].real)\n        cols.append(sigma[k][:, iu[0], iu[1]].imag)",
+         "cols.append(sigma[k][:, iu[0], iu[1]].imag)\n        cols.append(sigma[k][:, iu[0], iu[1]].real)"),
+    "Re and Im of the SVD coefficients swapped in the packing":
+        ("__init__.py", "cols.append(C[k, j].real)\n            cols.append(C[k, j].imag)",
+         "cols.append(C[k, j].imag)\n            cols.append(C[k, j].real)"),
+    "fit with a wider Gaussian than the evaluation":
+        ("__init__.py", "return np.exp(-s2)", "return np.exp(-0.5 * s2)"),
+    "fit with another multiquadric than the evaluation":
+        ("__init__.py", "return np.sqrt(1.0 + s2)", "return np.sqrt(2.0 + s2)"),
+    "cubic polyharmonic taken as order 1":
+        ("__init__.py", '"phs3": 2, "mq": 1', '"phs3": 1, "mq": 1'),
+    "radical inverse one digit short":
+        ("startup.py", "return num / den", "return num / (den * base)"),
+    "ellipsoid semi-axes from the eigenvalue instead of its inverse":
+        ("startup.py", "a = np.sqrt(mismatch / lam)", "a = np.sqrt(mismatch * lam)"),
+    "squeeze applied to the shortest axis":
+        ("startup.py", "a[0] *= squeeze", "a[3] *= squeeze"),
+    "data conjugated instead of the template":
+        ("startup.py", "4.0 * ws.df * np.conj(h) * d / psd", "4.0 * ws.df * h * np.conj(d) / psd"),
+    "time shifts from zero instead of centred":
+        ("startup.py", "idx = np.arange(-(M // 2), M - M // 2) % ws.L", "idx = np.arange(0, M) % ws.L"),
+    "cross terms conjugated":
+        ("startup.py", "S[k, n] = 4.0 * ws.df * (np.conj(h) @ hw.T)", "S[k, n] = 4.0 * ws.df * (h @ np.conj(hw).T)"),
+    "match normalised by one template only":
+        ("startup.py", "return float(np.abs(z).max() / math.sqrt(saa * sbb))",
+         "return float(np.abs(z).max() / saa)"),
+    "squeeze factor without the interpolation":
+        ("startup.py", "return prev_t + (t - prev_t) * (prev_m - target) / (prev_m - m)", "return t"),
+    "log-volume step of one live point for the whole batch":
+        ("nested.py", "lx_new = logX - 1.0 / (N - j)", "lx_new = logX - 1.0 / N"),
+    "splitmix64 multiplier off by one":
+        ("nested.py", "_M2 = np.uint64(0x94D049BB133111EB)", "_M2 = np.uint64(0x94D049BB133111EA)"),
+    "final live points without their share of the volume":
+        ("nested.py", "logw = L[i] + logX - math.log(N)", "logw = L[i] + logX"),
+    "closed-form evidence with two degrees of freedom":
+        ("nested.py", "cdf = -math.expm1(-0.5 * t) - math.exp(-0.5 * t) * 0.5 * t", "cdf = -math.expm1(-0.5 * t)"),
+    "Kish size without the square":
+        ("nested.py", "return float(w.sum() ** 2 / (w * w).sum())", "return float(w.sum() / (w * w).sum())"),
+    "distance uniform instead of uniform in volume":
+        ("nested.py", "ex[:, 0] = np.cbrt(self.d3[0] + v[:, 4] * (self.d3[1] - self.d3[0]))",
+         "ex[:, 0] = np.cbrt(self.d3[0]) + v[:, 4] * (np.cbrt(self.d3[1]) - np.cbrt(self.d3[0]))"),
+    "SiLU derivative taken as the sigmoid\'s":
+        ("mlp.py", "return s * (1.0 + z * (1.0 - s))", "return s * (1.0 - s)"),
+    "MSE gradient without the mean over outputs":
+        ("mlp.py", "g = 2.0 * (y - np.asarray(t, dtype=np.float64)) / (B * K)",
+         "g = 2.0 * (y - np.asarray(t, dtype=np.float64)) / B"),
+    "output layer activated":
+        ("mlp.py", "h = silu(z) if l < L - 1 else z", "h = silu(z)"),
+    "Adam without the second-moment bias correction":
+        ("mlp.py", "c2 = 1.0 - self.b2 ** self.t", "c2 = 1.0"),
+}
+
+
+def _run_python_mutant(relfile, text, tmp_dir, pin_files):
+    """A copy of the oracle package with `relfile` replaced by `text`,
+    imported ahead of the real one; the pin suites `pin_files` run on it."""
+    pkg = os.path.join(tmp_dir, "oracle")
+    shutil.copytree(os.path.join(ROOT, "oracle"), pkg, ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    with open(os.path.join(pkg, relfile), "w") as f:
+        f.write(text)
+    args = [*pin_files, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"]
+    code = (f"import sys; sys.path[:0] = [{tmp_dir!r}, {ROOT!r}]; "
+            "import oracle, oracle.startup, oracle.nested, oracle.mlp; "
+            f"assert oracle.__file__.startswith({tmp_dir!r}); "
+            f"import pytest; sys.exit(pytest.main({args!r}))")
+    env = dict(os.environ, MFORACLE_SO=oracle.build(), OMP_NUM_THREADS="2")
+    p = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True,
+                       timeout=900)
+    failed = re.findall(r"^FAILED (\S+)", p.stdout, flags=re.M)
+    return p.returncode, (failed[0] if failed else p.stdout[-600:] + p.stderr[-600:])
+
+
+def test_every_planted_mistake_in_the_numpy_oracle_fails_a_pin(tmp_path):
+    jobs = {"(unmutated)": ("__init__.py", open(os.path.join(ROOT, "oracle", "__init__.py")).read())}
+    for name, (rel, old, new) in PY_MUTANTS.items():
+        base = open(os.path.join(ROOT, "oracle", rel)).read()
+        assert base.count(old) == 1, f"{name}: the mutated text must occur once in oracle/{rel}"
+        jobs[name] = (rel, base.replace(old, new))
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(6, (os.cpu_count() or 2) // 2))) as ex:
+        futs = {}
+        for i, (name, (rel, text)) in enumerate(jobs.items()):
+            d = tmp_path / f"p{i}"
+            d.mkdir()
+            pins = ALL_PIN_FILES if name == "(unmutated)" else PINS_OF[rel]
+            futs[name] = ex.submit(_run_python_mutant, rel, text, str(d), pins)
         res = {name: f.result() for name, f in futs.items()}
     rc, info = res.pop("(unmutated)")
     assert rc == 0, f"the unmutated oracle fails its pins under the harness: {info}"

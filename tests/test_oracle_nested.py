@@ -7,7 +7,8 @@ any implementation to compare with:
   4-ball has the closed form (2 pi s^2)^2 P(chi^2_4 <= r^2 / s^2) / V_4(r)
   (for mu = 0), and the sampler's mean over seeds matches it within its
   own statistical error; the posterior mean and variance are mu and s^2;
-* N_eff = (sum w)^2 / sum w^2 is n for equal weights and 1 for one weight."""
+* N_eff = (sum w)^2 / sum w^2 is n for equal weights and 1 for one weight;
+* the distance prior is uniform in volume (the prior table of Sec. III A)."""
 import math
 
 import numpy as np
@@ -78,3 +79,22 @@ def test_library_reweight_matches_kish_formula():
     assert abs(ne - 64) < 1e-9
     w, ne = mf.reweight(np.array([0.0, -1e4, -1e4]))
     assert abs(ne - 1) < 1e-9
+
+
+def test_prior_distance_uniform_in_volume():
+    """The prior table of Sec. III A draws d_L uniformly in volume: the
+    sampler's unit coordinate u maps to d_L with P(d_L <= D) = u, i.e.
+    (D^3 - d_min^3) / (d_max^3 - d_min^3) = u; cos(iota) and the other
+    extrinsic rows pass through unchanged."""
+    d_min, d_max = 100.0, 400.0
+    pr = ns.Prior(9, 0.9, d_min, d_max, 5e-3)
+    u = np.linspace(0.0, 1.0, 11)
+    v = np.zeros((u.size, 9))
+    v[:, 4] = u
+    v[:, 5:9] = np.array([0.25, 1.0, 2.0, 1e-3])
+    _, ex = pr.to_query(v, np.eye(4), np.zeros(4), 5)
+    d = ex[:, 0].astype(np.float64)
+    cdf = (d ** 3 - d_min ** 3) / (d_max ** 3 - d_min ** 3)
+    assert np.abs(cdf - u).max() < 1e-5                     # FP32 rows
+    assert abs(d[0] - d_min) < 1e-4 and abs(d[-1] - d_max) < 1e-4
+    assert np.allclose(ex[:, 1:5], np.float32([0.25, 1.0, 2.0, 1e-3]))

@@ -5,15 +5,18 @@ fixed independently of it:
   and 3); the selected points lie in the unit ball and fill it uniformly
   (radius CDF r^4);
 * nodes lie in the (squeezed) constant-match ellipsoid x^T g x <= mismatch
-  (Eq. MisMatch) and the frame maps them back to the whitened points;
+  (Eq. MisMatch), fill it along every eigenvector of the metric, the longest
+  axis alone shortened by the squeeze factor, and the frame maps them back
+  to the whitened points;
 * the FFT overlaps equal the directly summed inverse DFT at any shift, a
   template against itself peaks at zero shift with the value sigma (real),
   and |z| never exceeds sqrt(sigma_hh sigma_dd) (Cauchy-Schwarz); sigma is
-  Hermitian positive semi-definite (Eq. conjugation_symmetry);
+  Hermitian positive semi-definite (Eq. conjugation_symmetry) and each
+  sigma_{mu nu} is the zero-shift overlap of template mu against template nu;
 * the oracle's template and the workload's injection, written separately,
   agree; the metric predicts 1 - match for small steps along its
   well-measured axes; the squeeze factor is where the true match reaches
-  the ellipsoid's match value."""
+  the ellipsoid's match value, to the accuracy of its interpolation."""
 import math
 
 import numpy as np
@@ -50,6 +53,13 @@ def test_nodes_in_squeezed_ellipsoid():
     R, a = su.ellipsoid_axes(ev.metric, ev.mismatch, 0.8)
     x = d @ R.T                                         # eigenbasis coordinates
     assert np.abs(x[:, 0]).max() <= a[0] * (1 + 1e-12)
+    # extent along each eigenvector of the metric (eigh here, ascending): the
+    # squeeze shortens the longest axis (smallest eigenvalue) only
+    lam, V = np.linalg.eigh(ev.metric)
+    theta4k, _, _ = su.place_nodes(ev.metric, ev.centre, ev.mismatch, 0.8, 4000)
+    ext = np.abs((theta4k - ev.centre) @ V).max(0) / np.sqrt(ev.mismatch / lam)
+    assert 0.95 * 0.8 < ext[0] <= 0.8 * (1 + 1e-12), ext
+    assert np.all((ext[1:] > 0.95) & (ext[1:] <= 1 + 1e-12)), ext
 
 
 def test_fft_overlap_equals_direct_sum():
@@ -78,6 +88,12 @@ def test_self_overlap_peaks_at_sigma_and_bounds():
     z = Z[0, 0, 0]                                       # mode 0 of the template against mode-0 data
     assert abs(z[128] - sig[0, 0]) < 1e-10 * abs(sig[0, 0]) and abs(z[128].imag) < 1e-10 * abs(sig[0, 0])
     assert np.abs(z).max() <= abs(sig[0, 0]) * (1 + 1e-12)
+    # sigma_{mu nu} = <h_mu|h_nu>: the zero-shift overlap of template mu
+    # against data equal to template nu (the FFT path), for every pair
+    for mu in range(len(ws.modes)):
+        for nu in range(len(ws.modes)):
+            z0 = su.overlap_series(ws, h[mu], h[nu], psd, 8)[4]
+            assert abs(z0 - sig[mu, nu]) <= 1e-12 * np.abs(sig).max(), (mu, nu)
 
 
 def test_template_matches_workload_injection():
@@ -104,4 +120,7 @@ def test_squeeze_factor_reaches_target_match():
     assert 0.5 < k < 1.0
     R, a = su.ellipsoid_axes(ev.metric, ev.mismatch)
     m = su.match22(ev.ws, ev.psd[0], ev.centre, ev.centre + R[0] * k * a[0])
-    assert abs(m - (1 - ev.mismatch)) < 2e-3
+    # the crossing is interpolated between grid points 1/64 apart: the match
+    # there is within the interpolation error (~1e-5), far below the match's
+    # change over one grid step (~2e-4 at the crossing)
+    assert abs(m - (1 - ev.mismatch)) < 3e-5
