@@ -85,6 +85,43 @@ MUTANTS = {
     "right ascension added to the hour angle":
         ("double h = m->gmst0 + m->omega_e * (tc + m->tau[k]) - alpha;",
          "double h = m->gmst0 + m->omega_e * (tc + m->tau[k]) + alpha;"),
+    "channel epoch left out of the Earth's rotation":
+        ("double h = m->gmst0 + m->omega_e * (tc + m->tau[k]) - alpha;",
+         "double h = m->gmst0 + m->omega_e * tc - alpha;"),
+    "frozen detector delay subtracted":
+        ("double t = (double)ext[4] + dtk;", "double t = (double)ext[4] - dtk;"),
+    "right ascension and declination swapped":
+        ("oracle_sky_response(m, k, ext[4], ext[5], ext[6], ext[2], &fp, &fx, &dtk);",
+         "oracle_sky_response(m, k, ext[4], ext[6], ext[5], ext[2], &fp, &fx, &dtk);"),
+    "natural instead of not-a-knot right end":
+        ("A[(n - 1) * n + n - 3] = 1.0; A[(n - 1) * n + n - 2] = -2.0; A[(n - 1) * n + n - 1] = 1.0;",
+         "A[(n - 1) * n + n - 1] = 1.0;"),
+    "spline evaluated mirrored in its interval":
+        ("double zr = oracle_spline(S, ys_re, half + u);\n            double zi = oracle_spline(S, ys_im, half + u);",
+         "double zr = oracle_spline(S, ys_re, half + 1 - u);\n            double zi = oracle_spline(S, ys_im, half + 1 - u);"),
+    "stencil window refused one sample early":
+        ("if (j - half < 0 || j - half + S - 1 > m->M - 1)", "if (j - half < 1 || j - half + S - 1 > m->M - 2)"),
+    "tail weights read in reverse order":
+        ("const double *w = m->W + (size_t)(m->N + p) * m->K;",
+         "const double *w = m->W + (size_t)(m->N + m->P - 1 - p) * m->K;"),
+    "imaginary part of (F+ - i Fx) conj(Y) with the wrong sign":
+        ("t2i = -fp * yp_im - fx * yp_re;", "t2i = fp * yp_im - fx * yp_re;"),
+    "inclination from asin":
+        ("double iota = acos(cosi);", "double iota = asin(cosi);"),
+    "ellipsoid centre added":
+        ("acc += m->R[i * 4 + j] * (theta[j] - m->centre[j]);", "acc += m->R[i * 4 + j] * (theta[j] + m->centre[j]);"),
+    "diagonal of Sigma read from the wrong columns":
+        ("sr[a * nm + a] = f[base + a];", "sr[a * nm + a] = f[base + nm - 1 - a];"),
+    "wave-frame Y axis with the wrong declination sign":
+        ("double Y0[3] = {-ch * sd, sh * sd, cd};", "double Y0[3] = {ch * sd, sh * sd, cd};"),
+    "source direction mirrored":
+        ("double w[3] = {cd * ch, -cd * sh, sd};", "double w[3] = {cd * ch, cd * sh, sd};"),
+    "cross polarisation tensor not symmetrised":
+        ("x += D[i * 3 + j] * (X[i] * Y[j] + Y[i] * X[j]);", "x += D[i * 3 + j] * (X[i] * Y[j]);"),
+    "cubic polyharmonic kernel as s^2":
+        ("case 1: return s2 * sqrt(s2);", "case 1: return s2;"),
+    "inverse multiquadric without the square root":
+        ("case 3: return 1.0 / sqrt(1.0 + s2);", "case 3: return 1.0 / (1.0 + s2);"),
 }
 
 

@@ -189,6 +189,34 @@ def test_lnl_at_node_matches_standin_and_hermitian_unpacking(oracle_mod):
         assert abs(got - (a * X - a * a * Y)) < 2e-4 * (1 + abs(a * X) + abs(a * a * Y))
 
 
+def test_detector_delay_shifts_the_overlap_time(oracle_mod):
+    """Detector k's overlap is read at t_c + dt_k (Sec. II D; Eq.
+    projected_h_fd): with delays and t_c on the sample grid, lnL at a node
+    equals a X - a^2 Y of the stand-in model with each z_k taken at
+    t_c + dt_k, where the spline reproduces the sample exactly."""
+    ev = make_event(spec_for("C1", N=300))
+    s = ev.spec
+    ev.det[:, 2] = np.array([3.0, -5.0, 7.0])[: s.n_det] * s.dt
+    m = oracle_mod.Model.from_event(ev)
+    tc = 2 * s.dt
+    rng = np.random.default_rng(6)
+    for idx in rng.choice(s.N, 3, replace=False):
+        theta = (ev.centre + ev.nodes[idx] @ ev.R0).astype(np.float32)
+        y32 = m.rotate(theta[None].astype(np.float64))[0]
+        ext = np.array([[150.0, -0.4, 2.2, 0.7, tc]], np.float32)
+        sig = standin.standin_sigma(ev, y32[None])[:, 0]
+        X = Y = 0.0
+        for k in range(s.n_det):
+            c1 = m.amplitudes(k, 100.0, float(ext[0, 1]), float(ext[0, 2]), float(ext[0, 3]))
+            t = np.array([tc + ev.det[k, 2]])
+            z = np.array([standin.standin_z(ev, k, j, y32[None], t)[0, 0] for j in range(s.n_modes)])
+            X += np.real(np.vdot(c1, z))
+            Y += 0.5 * np.real(np.vdot(c1, sig[k] @ c1))
+        a = 100.0 / 150.0
+        got = m.loglike(theta[None], ext)[0]
+        assert abs(got - (a * X - a * a * Y)) < 2e-4 * (1 + abs(a * X) + abs(a * a * Y))
+
+
 def test_lnl_quadratic_in_amplitude(oracle_mod):
     ev = make_event(spec_for("C1", N=200))
     m = oracle_mod.Model.from_event(ev)
@@ -282,6 +310,21 @@ def test_out_of_window_is_nan(oracle_mod):
     ex[2, 4] = -0.0157
     L = m.loglike(th, ex)
     assert np.isfinite(L[0]) and np.isnan(L[1]) and np.isnan(L[2]) and np.isfinite(L[3])
+
+
+def test_window_edges(oracle_mod):
+    """The ten-sample stencil j-4 .. j+5 (j = floor((t - t0) / dt)) must lie in
+    the sampled series: the first and last valid intervals give a finite lnL,
+    one sample beyond either gives NaN (times exact in FP32)."""
+    ev = make_event(spec_for("C0"))
+    m = oracle_mod.Model.from_event(ev)
+    s = ev.spec
+    th, ex = make_queries(ev, 4)
+    for q, samp in enumerate((4.5, 3.5, s.M - 5.5, s.M - 4.5)):
+        ex[q, 4] = np.float32(s.t0 + samp * s.dt)
+        assert float(ex[q, 4]) == s.t0 + samp * s.dt
+    L = m.loglike(th, ex)
+    assert np.isfinite(L[0]) and np.isnan(L[1]) and np.isfinite(L[2]) and np.isnan(L[3])
 
 
 @pytest.mark.slow
