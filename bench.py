@@ -61,7 +61,7 @@ def fp32_simt_peak(sm_max_mhz=None):
 
 
 def workload_name(spec) -> str:
-    """The workload string both arms print (the driver compares them)."""
+    """The workload string both arms print, so that their lines can be compared."""
     P = 5 if spec.tail_degree == 1 else (1 if spec.tail_degree == 0 else 0)
     return (f"{spec.name}: {spec.n_det} det x {spec.n_modes} modes, N={spec.N}+{P} nodes, "
             f"rank {spec.rank}, M={spec.M}, K={spec.K}, Q={spec.Q} per step per GPU")
@@ -295,7 +295,7 @@ def run_ours(args):
     for f in forms:
         try:
             m.set_form(f)
-        except Exception as e:  # form not available in this build
+        except Exception as e:  # form refused for this workload (e.g. an unbounded kernel in FP16)
             res[f] = {"error": str(e)}
             continue
         out = m.loglike(d_th, d_ex, out=d_out)
