@@ -1,7 +1,7 @@
 """bench.py's JSON-line contract, checked on the CPU through its reference arm
-(the FP64 oracle timed on the host cores): one line, the keys a reader of it
-reads, the same workload string as the GPU arm, zero copy bytes, and the
-replica helpers' whole-job arithmetic."""
+(the FP64 oracle timed on the host cores): one line carrying every key of
+the contract, the same workload string as the GPU arm, zero copy bytes, and
+the replica helpers' whole-job arithmetic."""
 import json
 import os
 import subprocess
