@@ -8,7 +8,8 @@ any implementation to compare with:
   (for mu = 0), and the sampler's mean over seeds matches it within its
   own statistical error; the posterior mean and variance are mu and s^2;
 * N_eff = (sum w)^2 / sum w^2 is n for equal weights and 1 for one weight;
-* the distance prior is uniform in volume (the prior table of Sec. III A)."""
+* the distance prior is uniform in volume (the injections' law in the table
+  of Sec. III A)."""
 import math
 
 import numpy as np
@@ -82,8 +83,10 @@ def test_library_reweight_matches_kish_formula():
 
 
 def test_prior_distance_uniform_in_volume():
-    """The prior table of Sec. III A draws d_L uniformly in volume: the
-    sampler's unit coordinate u maps to d_L with P(d_L <= D) = u, i.e.
+    """The sampler's distance prior is uniform in volume, the distribution
+    of the injections in the table of Sec. III A (the paper's own runs took
+    d_L uniform over [10, 1000] Mpc instead, per the table's caption): the
+    unit coordinate u maps to d_L with P(d_L <= D) = u, i.e.
     (D^3 - d_min^3) / (d_max^3 - d_min^3) = u; cos(iota) and the other
     extrinsic rows pass through unchanged."""
     d_min, d_max = 100.0, 400.0
