@@ -393,3 +393,38 @@ def test_lnl_from_columns_at_nodes_matches_standin(oracle_mod):
     th, ex = make_queries(ev, 50, seed=91)
     F = m.rbf_eval(m.rotate(th.astype(np.float64)))
     assert np.allclose(oracle_mod.loglike_columns(m, F, ex), m.loglike(th, ex), rtol=0, atol=1e-9)
+
+
+def test_inner_product_counts_match_the_paper(oracle_mod):
+    """The paper's counts per detector (tests/golden/inner_products_per_detector.txt,
+    Sec. II C 2): n vector inner products, n^2 scalar ones of which
+    n(n+1)/2 are independent.  The oracle's column packing holds, per
+    detector, n x 2l reals of SVD coefficients and n^2 reals of sigma (the
+    n real diagonals plus Re and Im of the n(n-1)/2 strict upper entries),
+    which rebuild the whole Hermitian sigma."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "inner_products_per_detector.txt")
+    rows = [list(map(int, ln.split())) for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert rows == [[5, 5, 25, 15]]
+    n, n_vec, n_scalar, n_indep = rows[0]
+    rng = np.random.default_rng(11)
+    N, l = 7, 3
+    C = rng.standard_normal((1, n, N, l)) + 1j * rng.standard_normal((1, n, N, l))
+    G = rng.standard_normal((N, n, n)) + 1j * rng.standard_normal((N, n, n))
+    sigma = (G @ np.conj(np.transpose(G, (0, 2, 1))))[None]      # Hermitian per node
+    F = oracle_mod.pack_node_values(C, sigma)
+    assert C.shape[1] == n_vec and sigma.shape[2] * sigma.shape[3] == n_scalar
+    assert F.shape == (N, n_vec * 2 * l + n_scalar)
+    iu = np.triu_indices(n)
+    assert len(iu[0]) == n_indep == n * (n + 1) // 2
+    # rebuild sigma from its n^2 packed reals
+    base = n * 2 * l
+    diag = F[:, base:base + n]
+    up = np.triu_indices(n, 1)
+    nup = len(up[0])
+    re_up, im_up = F[:, base + n:base + n + nup], F[:, base + n + nup:base + n + 2 * nup]
+    S = np.zeros((N, n, n), complex)
+    S[:, np.arange(n), np.arange(n)] = diag
+    S[:, up[0], up[1]] = re_up + 1j * im_up
+    S[:, up[1], up[0]] = re_up - 1j * im_up
+    assert np.allclose(S, sigma[0], rtol=0, atol=1e-12 * np.abs(sigma).max())
