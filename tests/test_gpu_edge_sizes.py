@@ -167,6 +167,7 @@ def test_batch_member_with_fewer_node_blocks_than_passes():
     finally:
         if b is not None:
             b.close()                     # before its members
+        big.set_option("pass_count", 0)   # the batch fixed its members' pass count: back to automatic
         big.set_form("fp32")
         tiny.close()
     for (m, om, _, q), (th, ex), g, s in zip(members, hq, got, single):
